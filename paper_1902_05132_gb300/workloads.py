@@ -1,0 +1,65 @@
+"""Seeded synthetic workloads shaped like the paper's experiments.
+
+This module holds no arithmetic of the method: it only describes media and
+draws particle positions and charges from a seeded generator.  It is shared
+by the tests, the benchmark and the oracle-side checks.
+
+Each workload returns a dict with keys
+  k, d, eps      -- wave numbers (top to bottom), interfaces, material coefficients
+  p, leaf        -- expansion order and leaf size
+  src, q, tgt    -- float64 [N,3] sources, complex128 [N] charges, targets
+"""
+import numpy as np
+
+
+def _cube(rng, n, zlo, zhi):
+    x = rng.uniform(-1.0, 1.0, n)
+    y = rng.uniform(-1.0, 1.0, n)
+    z = rng.uniform(zlo, zhi, n)
+    return np.stack([x, y, z], axis=1)
+
+
+def _split(n, parts):
+    base = n // parts
+    out = [base] * parts
+    for i in range(n - base * parts):
+        out[i] += 1
+    return out
+
+
+def two_layer(n=1000, seed=0, p=5, leaf=40):
+    """Two layers, interface z = 0, k = (1.0, 1.5), eps = (1, 2); half the
+    points uniform in [-1,1]^2 x [0.1,1.1], half in [-1,1]^2 x [-1.1,-0.1];
+    real charges U[0,1]; targets = sources."""
+    rng = np.random.default_rng(seed)
+    n0, n1 = _split(n, 2)
+    src = np.concatenate([_cube(rng, n0, 0.1, 1.1), _cube(rng, n1, -1.1, -0.1)])
+    q = rng.uniform(0.0, 1.0, n).astype(complex)
+    return dict(k=[1.0, 1.5], d=[0.0], eps=[1.0, 2.0], p=p, leaf=leaf,
+                src=src, q=q, tgt=src.copy(), name=f"two-layer N={n} p={p} leaf={leaf}")
+
+
+THREE_LAYER_CUBES = ((0.1, 1.1), (-1.1, -0.1), (-2.3, -1.3))
+
+
+def three_layer(n=32768, seed=0, p=8, leaf=64, complex_charges=False):
+    """Three layers, interfaces z = 0 and -1.2, k = (0.8, 1.2, 1.6),
+    eps = (1, 2, 3); n points split evenly over the cubes [-1,1]^2 x
+    {[0.1,1.1], [-1.1,-0.1], [-2.3,-1.3]}; charges U[0,1] (or complex with
+    Re, Im ~ U[-1,1]); targets = sources."""
+    rng = np.random.default_rng(seed)
+    parts = _split(n, 3)
+    src = np.concatenate([_cube(rng, m, lo, hi) for m, (lo, hi) in zip(parts, THREE_LAYER_CUBES)])
+    if complex_charges:
+        q = rng.uniform(-1.0, 1.0, n) + 1j * rng.uniform(-1.0, 1.0, n)
+    else:
+        q = rng.uniform(0.0, 1.0, n).astype(complex)
+    return dict(k=[0.8, 1.2, 1.6], d=[0.0, -1.2], eps=[1.0, 2.0, 3.0], p=p, leaf=leaf,
+                src=src, q=q, tgt=src.copy(), name=f"three-layer N={n} p={p} leaf={leaf}")
+
+
+def sample_targets(n, count, seed=1):
+    """Seeded sample of target indices (sorted, distinct)."""
+    rng = np.random.default_rng(seed)
+    count = min(count, n)
+    return np.sort(rng.choice(n, size=count, replace=False))
