@@ -1,0 +1,159 @@
+/*
+ * fmm_layered.h -- C ABI of the GB300 layered-media Helmholtz FMM.
+ *
+ * Computes, for N_t targets and N_s wave sources embedded in a medium of
+ * L+1 horizontal layers, the potentials
+ *
+ *     Phi(t_i) = sum_j q_j G(t_i, s_j)
+ *
+ * with G the layered-media Green's function of the Helmholtz equation
+ * (Wang, Zhang & Cai, "Fast multipole method for 3-D Helmholtz equation in
+ * layered media", Sec. 3.1 eqs. domaingreenfn-totaldensity and the sum of
+ * eq. totalinteraction): the free-space part e^{ik_l r}/(4 pi r) for source
+ * and target in the same layer l (skipped when the two points are bitwise
+ * identical, the paper's j != i), plus the reaction components u^{ab}_{l l'}
+ * for every source (self image included).  Interface conditions: [u] = 0 and
+ * [eps du/dz] = 0 across every interface.
+ *
+ * Layers are numbered 0..L from top to bottom; interfaces d_0 > ... > d_{L-1};
+ * layer l is d_l < z < d_{l-1}.
+ *
+ * Memory and threading: the caller owns every buffer passed in.  The library
+ * owns the handle and its device workspace (grown on demand, freed by
+ * fmm_layered_destroy).  A handle must not be used by two threads at once.
+ * Device buffers must be on the device that was current at create time.
+ *
+ * Errors: every int-returning call returns 0 (FMM_OK) or a negative code;
+ * fmm_layered_last_error() then describes the last failure of that handle.
+ */
+#ifndef FMM_LAYERED_H
+#define FMM_LAYERED_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMM_OK                 0
+#define FMM_ERR_ARG           -1   /* invalid argument (sizes, order, layers) */
+#define FMM_ERR_ON_INTERFACE  -2   /* a point lies exactly on an interface    */
+#define FMM_ERR_NONFINITE     -3   /* a coordinate or charge is NaN or Inf    */
+#define FMM_ERR_CUDA          -4   /* a CUDA call failed                      */
+#define FMM_ERR_OOM           -5   /* device allocation failed                */
+#define FMM_ERR_TIMEOUT       -6   /* reserved: bounded device wait expired   */
+#define FMM_ERR_UNSUPPORTED   -7   /* beyond the compiled limits              */
+
+/* flags for fmm_layered_create */
+#define FMM_PLAIN_FP64   0u   /* every stage in FP64 (default)                 */
+#define FMM_NORM_PAPER   1u   /* scale results for targets in layer l by
+                                 4 pi / (i k_l): the paper's h_0 normalization
+                                 with the factor i k_l / 4 pi omitted (eq.
+                                 totalinteraction)                             */
+
+typedef struct fmm_layered fmm_layered_t;
+
+typedef struct {
+  int    n_components;     /* FMMs in the last evaluation (free + reaction)  */
+  int    n_boxes;          /* boxes over all component trees                 */
+  int    max_level;        /* deepest tree level                             */
+  long   n_v_pairs;        /* M2L translations                               */
+  long   n_u_pairs;        /* near-field (U, W, X) source-target pairs       */
+  int    n_quad_near;      /* complex contour nodes of the quadrature rule   */
+  int    n_quad_total;     /* all contour nodes currently held               */
+  double ms_setup;         /* last fmm_layered_create, host wall clock       */
+  double ms_tree;          /* last evaluation: classification, keys, sort,
+                              levels and lists (host wall clock, synchronous) */
+  double ms_operators;     /* translation operators                          */
+  double ms_eval;          /* upward, downward, near field and sum           */
+} fmm_stats_t;
+
+/*
+ * Create a solver for a layered medium (Sec. 3.1).
+ *   n_layers    L+1 >= 1 (at most 8)
+ *   k           [L+1] wave numbers k_l > 0, top to bottom (host)
+ *   interfaces  [L] d_0 > d_1 > ... (host; NULL when L = 0)
+ *   eps         [L+1] material coefficients > 0 in the transmission
+ *               condition [eps du/dz] = 0 (host; NULL means all 1)
+ *   p           expansion order, 1 <= p <= 20 (terms n = 0..p)
+ *   leaf        maximum number of sources or targets in a leaf box, >= 1
+ *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER
+ *   out         receives the handle (NULL on failure)
+ * Builds the contour quadrature rule and the reaction densities sigma at its
+ * nodes on the current device.  Returns FMM_ERR_ARG for invalid input.
+ */
+int fmm_layered_create(int n_layers, const double* k, const double* interfaces,
+                       const double* eps, int p, int leaf, unsigned flags,
+                       fmm_layered_t** out);
+
+/* Release the handle and all device memory it owns.  NULL is accepted. */
+void fmm_layered_destroy(fmm_layered_t* h);
+
+/* Message of the handle's last failure ("" if none); valid until the next
+ * call on the handle.  With h == NULL: message of the last failed create. */
+const char* fmm_layered_last_error(const fmm_layered_t* h);
+
+/*
+ * FMM evaluation (Algorithm 1 for every component, summed as in eq.
+ * totalinteraction).
+ *   src_xyz   [n_src*3] row-major x,y,z (device)
+ *   charges   [2*n_src] interleaved complex128 (device)
+ *   tgt_xyz   [n_tgt*3] (device)
+ *   out       [2*n_tgt] interleaved complex128 potentials (device, written)
+ *   stream    cudaStream_t to run on (NULL: legacy default stream)
+ * The call returns after the result is complete on `stream` (it synchronizes
+ * the stream while building the trees).  n_src or n_tgt may be 0.
+ * FMM_ERR_ON_INTERFACE if a point has z equal to an interface;
+ * FMM_ERR_NONFINITE for NaN/Inf input.
+ */
+int fmm_layered_eval(fmm_layered_t* h, long n_src, const double* src_xyz,
+                     const double* charges, long n_tgt, const double* tgt_xyz,
+                     double* out, void* stream);
+
+/* Same as fmm_layered_eval with HOST buffers: copies inputs to the device,
+ * evaluates and copies the potentials back (all on `stream`). */
+int fmm_layered_eval_host(fmm_layered_t* h, long n_src, const double* src_xyz,
+                          const double* charges, long n_tgt, const double* tgt_xyz,
+                          double* out, void* stream);
+
+/*
+ * Direct O(N_s N_t) evaluation of the same sum on the GPU: free-space kernel
+ * and the reaction part as one Sommerfeld integral per pair on the library's
+ * contour (eq. generalcomponents summed over the four types).  Arguments as
+ * fmm_layered_eval (device buffers).
+ */
+int fmm_layered_direct(fmm_layered_t* h, long n_src, const double* src_xyz,
+                       const double* charges, long n_tgt, const double* tgt_xyz,
+                       double* out, void* stream);
+
+/* Statistics of the last create/evaluation. */
+int fmm_layered_stats(const fmm_layered_t* h, fmm_stats_t* stats);
+
+/*
+ * Export of the trees and interaction lists of the last evaluation, for
+ * checking them against an independent implementation.
+ *   fmm_layered_component_info: for component c (0 <= c < n_components, in the
+ *     order: free-space layers 0..L, then reaction (l, l', a, b) in
+ *     lexicographic order with arrow up = 0, down = 1) writes
+ *     info[0..9] = kind (0 free, 1 reaction), l, l', a, b, n_src, n_tgt,
+ *     n_boxes, n_levels, 0 and root[0..3] = centre x, y, z and half-width.
+ *   fmm_layered_tree_export: host arrays sized by component_info; boxes are
+ *     numbered per component by (level, key prefix):
+ *       level[nb], prefix[nb] (uint64 as long long), src_begin[nb],
+ *       src_end[nb], tgt_begin[nb], tgt_end[nb], parent[nb] (component-local
+ *       positions; -1 for the root),
+ *       src_perm[n_src], tgt_perm[n_tgt]: original index (within the
+ *       component's layer) of each sorted point,
+ *       list_off[4][nb+1], list_idx[4][*]: CSR of the V, U, W, X lists
+ *       (list_idx arrays sized by list_off[..][nb]; pass NULL list_idx to only
+ *       read the offsets).
+ */
+int fmm_layered_num_components(const fmm_layered_t* h);
+int fmm_layered_component_info(const fmm_layered_t* h, int c, long long* info, double* root);
+int fmm_layered_tree_export(const fmm_layered_t* h, int c, int* level, long long* prefix,
+                            int* src_begin, int* src_end, int* tgt_begin, int* tgt_end,
+                            int* parent, int* src_perm, int* tgt_perm,
+                            int* list_off, int* v_idx, int* u_idx, int* w_idx, int* x_idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

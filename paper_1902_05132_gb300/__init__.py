@@ -1,0 +1,191 @@
+"""GB300 layered-media Helmholtz FMM: thin ctypes binding of libfmmlayered.so.
+
+Argument marshalling only: every step of the evaluation runs in the library's
+CUDA kernels.  The library is built in-tree by ``_build.build()``; importing
+this package does not build it, and every call fails loudly if it is missing.
+
+Tensors: positions float64 [N, 3] (row-major), charges complex128 [N],
+results complex128 [N], all on the CUDA device the solver was created on
+(``eval``/``direct``), or numpy arrays in host memory (``eval_host``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmmlayered.so")
+
+FMM_PLAIN_FP64 = 0
+FMM_NORM_PAPER = 1
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "point on an interface", -3: "non-finite input",
+          -4: "CUDA error", -5: "out of device memory", -6: "timeout", -7: "unsupported"}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_components", ctypes.c_int), ("n_boxes", ctypes.c_int), ("max_level", ctypes.c_int),
+                ("n_v_pairs", ctypes.c_long), ("n_u_pairs", ctypes.c_long), ("n_quad_near", ctypes.c_int),
+                ("n_quad_total", ctypes.c_int), ("ms_setup", ctypes.c_double), ("ms_tree", ctypes.c_double),
+                ("ms_operators", ctypes.c_double), ("ms_eval", ctypes.c_double)]
+
+
+EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
+            "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
+            "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export"]
+
+_lib = None
+
+
+def lib():
+    """Load libfmmlayered.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1902_05132_gb300._build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    d, i, l, v, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_void_p, ctypes.c_uint
+    L.fmm_layered_create.argtypes = [i, d, d, d, i, i, u, ctypes.POINTER(ctypes.c_void_p)]
+    L.fmm_layered_create.restype = i
+    L.fmm_layered_destroy.argtypes = [v]
+    L.fmm_layered_destroy.restype = None
+    L.fmm_layered_last_error.argtypes = [v]
+    L.fmm_layered_last_error.restype = ctypes.c_char_p
+    for name in ("fmm_layered_eval", "fmm_layered_eval_host", "fmm_layered_direct"):
+        f = getattr(L, name)
+        f.argtypes = [v, l, d, d, l, d, d, v]
+        f.restype = i
+    L.fmm_layered_stats.argtypes = [v, ctypes.POINTER(Stats)]
+    L.fmm_layered_stats.restype = i
+    L.fmm_layered_num_components.argtypes = [v]
+    L.fmm_layered_num_components.restype = i
+    L.fmm_layered_component_info.argtypes = [v, i, d, d]
+    L.fmm_layered_component_info.restype = i
+    L.fmm_layered_tree_export.argtypes = [v, i] + [d] * 14
+    L.fmm_layered_tree_export.restype = i
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class LayeredFMM:
+    """Solver for one layered medium (Sec. 3.1): wave numbers k (top to bottom),
+    interfaces d (descending), material coefficients eps, order p, leaf size."""
+
+    def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False):
+        L = lib()
+        self.k = np.ascontiguousarray(k, dtype=np.float64)
+        self.d = np.ascontiguousarray(d, dtype=np.float64)
+        self.eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+        self.p, self.leaf = int(p), int(leaf)
+        h = ctypes.c_void_p()
+        rc = L.fmm_layered_create(len(self.k), _ptr(self.k), _ptr(self.d) if len(self.d) else None,
+                                  _ptr(self.eps), self.p, self.leaf,
+                                  FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64, ctypes.byref(h))
+        if rc != 0:
+            raise FmmError(rc, L.fmm_layered_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fmm_layered_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise FmmError(rc, lib().fmm_layered_last_error(self.h).decode())
+
+    @staticmethod
+    def _dev_args(src, q, tgt):
+        import torch
+        src = src.contiguous()
+        tgt = tgt.contiguous()
+        qr = torch.view_as_real(q.contiguous()).contiguous()
+        return src, qr, tgt
+
+    def _call_dev(self, fn, src, q, tgt, out, stream):
+        import torch
+        src, qr, tgt = self._dev_args(src, q, tgt)
+        if out is None:
+            out = torch.empty(tgt.shape[0], dtype=torch.complex128, device=tgt.device)
+        outr = torch.view_as_real(out)
+        if stream is None:
+            stream = torch.cuda.current_stream(tgt.device)
+        self._check(fn(self.h, src.shape[0], _ptr(src), _ptr(qr), tgt.shape[0], _ptr(tgt), _ptr(outr),
+                       ctypes.c_void_p(stream.cuda_stream)))
+        return out
+
+    def eval(self, src, q, tgt, out=None, stream=None):
+        """FMM potentials at tgt (device tensors)."""
+        return self._call_dev(lib().fmm_layered_eval, src, q, tgt, out, stream)
+
+    def direct(self, src, q, tgt, out=None, stream=None):
+        """All-pairs direct sum on the GPU (device tensors)."""
+        return self._call_dev(lib().fmm_layered_direct, src, q, tgt, out, stream)
+
+    def eval_host(self, src, q, tgt, stream=None):
+        """FMM with host (numpy) buffers: copies in, evaluates, copies back."""
+        src = np.ascontiguousarray(src, dtype=np.float64)
+        tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+        qr = np.ascontiguousarray(np.asarray(q, dtype=np.complex128)).view(np.float64)
+        out = np.empty(2 * len(tgt), dtype=np.float64)
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(lib().fmm_layered_eval_host(self.h, len(src), _ptr(src), _ptr(qr), len(tgt), _ptr(tgt),
+                                                _ptr(out), st))
+        return out.view(np.complex128)
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().fmm_layered_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def trees(self):
+        """Trees and lists of the last evaluation, one dict per component."""
+        L = lib()
+        out = []
+        for c in range(L.fmm_layered_num_components(self.h)):
+            info = np.zeros(10, dtype=np.int64)
+            root = np.zeros(4, dtype=np.float64)
+            self._check(L.fmm_layered_component_info(self.h, c, _ptr(info), _ptr(root)))
+            kind, l, lp, a, b, ns, nt, nb, nlev, _ = (int(x) for x in info)
+            arr = {name: np.zeros(nb, dtype=np.int32) for name in
+                   ("level", "src_begin", "src_end", "tgt_begin", "tgt_end", "parent")}
+            prefix = np.zeros(nb, dtype=np.int64)
+            sperm = np.zeros(max(ns, 1), dtype=np.int32)
+            tperm = np.zeros(max(nt, 1), dtype=np.int32)
+            off = np.zeros(4 * (nb + 1), dtype=np.int32)
+            self._check(L.fmm_layered_tree_export(self.h, c, _ptr(arr["level"]), _ptr(prefix), _ptr(arr["src_begin"]),
+                                                  _ptr(arr["src_end"]), _ptr(arr["tgt_begin"]), _ptr(arr["tgt_end"]),
+                                                  _ptr(arr["parent"]), _ptr(sperm), _ptr(tperm), _ptr(off),
+                                                  None, None, None, None))
+            off = off.reshape(4, nb + 1)
+            idx = [np.zeros(max(int(off[k, nb]), 1), dtype=np.int32) for k in range(4)]
+            self._check(L.fmm_layered_tree_export(self.h, c, None, None, None, None, None, None, None, None, None,
+                                                  _ptr(off), *(_ptr(x) for x in idx)))
+            lists = {}
+            for k, name in enumerate("VUWX"):
+                lists[name] = {bx: idx[k][off[k, bx]:off[k, bx + 1]].tolist()
+                               for bx in range(nb) if off[k, bx + 1] > off[k, bx]}
+            out.append(dict(kind=kind, l=l, lp=lp, a=a, b=b, ns=ns, nt=nt, root=root, prefix=prefix.view(np.uint64),
+                            sperm=sperm[:ns], tperm=tperm[:nt], lists=lists, **arr))
+        return out

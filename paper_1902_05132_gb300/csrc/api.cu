@@ -1,0 +1,615 @@
+// C ABI and host orchestration of one evaluation (Algorithm 1 for every
+// component, summed as in eq. totalinteraction).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fmm_internal.h"
+
+// ---- launchers of the other translation units
+void launch_gaunt(int p, const std::vector<double>& xg, const std::vector<double>& wg, double* G, double* dx,
+                  double* dw, cudaStream_t st);
+void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st);
+void launch_reac_T(int p, const ReacJob* jobs, int njobs, const Rule& R, cplx* ops, cudaStream_t st);
+void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
+                const cplx* sq, cplx* M, cudaStream_t st);
+void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, const cplx* ops, cplx* M,
+                cudaStream_t st);
+void launch_m2l(int p, const int* boxes, int n, int with_l2l, BoxGeom B, OpIndex OI, const int* voff,
+                const int* vidx, const cplx* m2l_ops, const cplx* l2l_ops, const cplx* M, cplx* L, int* err,
+                cudaStream_t st);
+void launch_phase_expand(int p, const ExpandJob* jobs, int njobs, const cplx* src, cplx* dst, cudaStream_t st);
+void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
+                const cplx* L, cplx* phi, cudaStream_t st);
+void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st);
+RuleView make_rule_view(const Rule& R, const cplx* coef);
+void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
+                 const cplx* sq, const double* tpos, cplx* phi, cudaStream_t st);
+void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
+                   RuleView R, const cplx* coef_all, double* out, cudaStream_t st);
+void launch_scatter_add(long n, const int* tidx, const cplx* phi, double* out, cudaStream_t st);
+void launch_norm_paper(long n, const double* tgt, DirectMedium md, double* out, cudaStream_t st);
+void build_trees(fmm_layered* h, long ns, const double* src, const double* q, long nt, const double* tgt,
+                 std::vector<double>& gap_out, cudaStream_t st);
+void tree_host_copy(fmm_layered* h, std::vector<int>& comp, std::vector<int>& lev,
+                    std::vector<unsigned long long>& prefix, std::vector<int>& sb, std::vector<int>& se,
+                    std::vector<int>& tb, std::vector<int>& te, std::vector<int>& parent);
+
+static thread_local std::string g_create_err;
+
+using Clock = std::chrono::steady_clock;
+static double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+template <class T>
+static T* need(DevBuf& b, size_t n) {
+  b.ensure(sizeof(T) * (n ? n : 1));
+  return b.as<T>();
+}
+template <class T>
+static T* upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+  T* p = need<T>(b, v.size());
+  if (!v.empty()) FMM_CHECK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return p;
+}
+
+// ---------------------------------------------------------------- create
+static void create_impl(fmm_layered* h) {
+  FMM_CHECK(cudaGetDevice(&h->dev));
+  upload(h->d_k, h->k, 0);
+  std::vector<double> dd = h->d;
+  if (dd.empty()) dd.push_back(0.0);
+  upload(h->d_d, dd, 0);
+  upload(h->d_eps, h->eps, 0);
+  rule_init(h);
+  // Gaunt table
+  int p = h->p, P = (p + 1) * (p + 1);
+  std::vector<double> xg, wg;
+  gauss_legendre_pub(2 * p + 2, xg, wg);
+  double* G = need<double>(h->tab.gaunt, (size_t)P * P * (2 * p + 1));
+  DevBuf tmpx, tmpw;
+  double* dx = need<double>(tmpx, xg.size());
+  double* dw = need<double>(tmpw, wg.size());
+  launch_gaunt(p, xg, wg, G, dx, dw, 0);
+  FMM_CHECK(cudaGetLastError());
+  FMM_CHECK(cudaStreamSynchronize(0));
+  tmpx.release();
+  tmpw.release();
+}
+
+extern "C" int fmm_layered_create(int n_layers, const double* k, const double* interfaces, const double* eps,
+                                  int p, int leaf, unsigned flags, fmm_layered_t** out) {
+  if (out) *out = nullptr;
+  g_create_err.clear();
+  if (!out || n_layers < 1 || n_layers > FMM_MAXL || !k || (n_layers > 1 && !interfaces) || p < 1 ||
+      p > 16 || leaf < 1) {
+    g_create_err = "invalid argument (layers in [1,8], p in [1,16], leaf >= 1, k and interfaces given)";
+    return FMM_ERR_ARG;
+  }
+  for (int l = 0; l < n_layers; ++l) {
+    if (!(k[l] > 0) || !std::isfinite(k[l]) || (eps && (!(eps[l] > 0) || !std::isfinite(eps[l])))) {
+      g_create_err = "wave numbers and material coefficients must be positive and finite";
+      return FMM_ERR_ARG;
+    }
+  }
+  for (int j = 0; j + 1 < n_layers; ++j) {
+    if (!std::isfinite(interfaces[j]) || (j > 0 && !(interfaces[j] < interfaces[j - 1]))) {
+      g_create_err = "interfaces must be finite and strictly decreasing";
+      return FMM_ERR_ARG;
+    }
+  }
+  auto t0 = Clock::now();
+  fmm_layered* h = new fmm_layered();
+  h->L1 = n_layers;
+  h->k.assign(k, k + n_layers);
+  h->d.assign(interfaces ? interfaces : k, interfaces ? interfaces + (n_layers - 1) : k);
+  if (n_layers == 1) h->d.clear();
+  h->eps.assign(n_layers, 1.0);
+  if (eps) h->eps.assign(eps, eps + n_layers);
+  h->p = p;
+  h->leaf = leaf;
+  h->flags = flags;
+  try {
+    create_impl(h);
+  } catch (FmmError& e) {
+    g_create_err = e.msg;
+    fmm_layered_destroy(h);
+    return e.code;
+  }
+  h->stats.ms_setup = ms_since(t0);
+  h->stats.n_quad_near = h->rule.n_near;
+  h->stats.n_quad_total = h->rule.Q();
+  *out = h;
+  return FMM_OK;
+}
+
+extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
+  if (!h) return;
+  DevBuf* all[] = {&h->d_k, &h->d_d, &h->d_eps, &h->rule.kr, &h->rule.w, &h->rule.kz, &h->rule.sigma,
+                   &h->tab.gaunt};
+  for (DevBuf* b : all) b->release();
+  Workspace& ws = h->ws;
+  DevBuf* wsb[] = {&ws.slayer, &ws.tlayer, &ws.sorder, &ws.torder, &ws.iota, &ws.ltmp, &ws.counts, &ws.bbox,
+                   &ws.gap, &ws.flags, &ws.spos_u, &ws.sq_u, &ws.skey_u, &ws.sval_u, &ws.sidx_u, &ws.tpos_u,
+                   &ws.tkey_u, &ws.tval_u, &ws.tidx_u, &ws.skey, &ws.sperm, &ws.spos, &ws.sq, &ws.sidx,
+                   &ws.slocal, &ws.tkey, &ws.tperm, &ws.tpos, &ws.tidx, &ws.tlocal, &ws.segs, &ws.segl,
+                   &ws.bcomp, &ws.blevel, &ws.bprefix, &ws.bsb, &ws.bse, &ws.btb, &ws.bte, &ws.bparent,
+                   &ws.bchild0, &ws.bnchild, &ws.bcoord, &ws.lvlcnt, &ws.lvlscan, &ws.lvl_begin, &ws.lcnt,
+                   &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
+                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.cub_tmp};
+  for (DevBuf* b : wsb) b->release();
+  delete h;
+}
+
+extern "C" const char* fmm_layered_last_error(const fmm_layered_t* h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+extern "C" int fmm_layered_stats(const fmm_layered_t* h, fmm_stats_t* s) {
+  if (!h || !s) return FMM_ERR_ARG;
+  *s = h->stats;
+  return FMM_OK;
+}
+
+static DirectMedium medium_of(const fmm_layered* h) {
+  DirectMedium md{};
+  md.L1 = h->L1;
+  for (int l = 0; l < h->L1; ++l) md.k[l] = h->k[l];
+  for (size_t j = 0; j < h->d.size(); ++j) md.d[j] = h->d[j];
+  return md;
+}
+
+// reaction coefficients for the current rule: [(l,l',a,b)][q]
+static cplx* rule_coef(fmm_layered* h, cudaStream_t st) {
+  cplx* coef = need<cplx>(h->ws.op_tab, (size_t)h->L1 * h->L1 * 4 * h->rule.Q());
+  launch_coef(h->L1, h->rule, coef, st);
+  FMM_CHECK(cudaGetLastError());
+  return coef;
+}
+
+// ---------------------------------------------------------------- direct
+extern "C" int fmm_layered_direct(fmm_layered_t* h, long ns, const double* src, const double* q, long nt,
+                                  const double* tgt, double* out, void* stream) {
+  if (!h) return FMM_ERR_ARG;
+  h->err.clear();
+  if (ns < 0 || nt < 0 || (ns && (!src || !q)) || (nt && (!tgt || !out))) {
+    h->err = "invalid argument";
+    return FMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    if (nt == 0) return FMM_OK;
+    // tail long enough for the smallest vertical gap: classify on the device
+    std::vector<double> gap;
+    build_trees(h, ns, src, q, nt, tgt, gap, st);
+    double gmin = INFINITY, smin = INFINITY;
+    for (int l = 0; l < h->L1; ++l)
+      for (int sd = 0; sd < 2; ++sd) {
+        smin = fmin(smin, gap[(0 * h->L1 + l) * 2 + sd]);
+        gmin = fmin(gmin, gap[(1 * h->L1 + l) * 2 + sd]);
+      }
+    if (h->L1 > 1 && std::isfinite(gmin + smin)) rule_extend(h, h->rule.ta + 30.0 / (gmin + smin), st);
+    cplx* coef = rule_coef(h, st);
+    launch_direct(nt, tgt, ns, src, q, medium_of(h), make_rule_view(h->rule, coef), coef, out, st);
+    if (h->flags & FMM_NORM_PAPER) launch_norm_paper(nt, tgt, medium_of(h), out, st);
+    FMM_CHECK(cudaGetLastError());
+    FMM_CHECK(cudaStreamSynchronize(st));
+  } catch (FmmError& e) {
+    h->err = e.msg;
+    return e.code;
+  }
+  return FMM_OK;
+}
+
+// ---------------------------------------------------------------- eval
+static const int RHO2[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+static int rho2_index(int r2) {
+  for (int i = 0; i < 10; ++i) if (RHO2[i] == r2) return i;
+  return -1;
+}
+
+static void eval_impl(fmm_layered* h, long ns, const double* src, const double* q, long nt, const double* tgt,
+                      double* out, cudaStream_t st) {
+  Workspace& ws = h->ws;
+  const int p = h->p, P = (p + 1) * (p + 1);
+  const long PP = (long)P * P;
+  FMM_CHECK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * nt, st));
+  if (nt == 0 || ns == 0) return;
+  auto t0 = Clock::now();
+  std::vector<double> gap;
+  build_trees(h, ns, src, q, nt, tgt, gap, st);
+  const std::vector<Comp>& comps = h->comps;
+  const int nc = (int)comps.size();
+  const int nb = h->nboxes;
+  const std::vector<int>& lvl = h->lvl_begin;
+  int maxlev = 0;
+  while (maxlev + 1 < 22 && lvl[maxlev + 2] > lvl[maxlev + 1]) ++maxlev;
+  // host copies needed for scheduling
+  std::vector<int> bcomp(nb), bnchild(nb), bsb(nb), bse(nb), btb(nb), bte(nb);
+  FMM_CHECK(cudaMemcpyAsync(bcomp.data(), ws.bcomp.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bnchild.data(), ws.bnchild.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bsb.data(), ws.bsb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bse.data(), ws.bse.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(btb.data(), ws.btb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bte.data(), ws.bte.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  std::vector<int> uo(nb + 1);
+  FMM_CHECK(cudaMemcpyAsync(uo.data(), ws.loff.as<int>() + (nb + 1), 4 * (nb + 1), cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaStreamSynchronize(st));
+  h->stats.n_u_pairs = uo[nb];
+  // per component: levels present
+  std::vector<std::vector<char>> has_level(nc, std::vector<char>(23, 0));
+  for (int l = 0; l <= maxlev; ++l)
+    for (int b = lvl[l]; b < lvl[l + 1]; ++b) has_level[bcomp[b]][l] = 1;
+  h->stats.ms_tree = ms_since(t0);
+  // ---- operators
+  auto t1 = Clock::now();
+  std::vector<CompGeom> cg(nc);
+  int nfree = 0, nreac = 0;
+  for (int c = 0; c < nc; ++c) {
+    const Comp& C_ = comps[c];
+    for (int a = 0; a < 3; ++a) cg[c].lo[a] = C_.c[a] - C_.h;
+    cg[c].h2 = 2.0 * C_.h;
+    cg[c].ks = C_.ks;
+    cg[c].kt = C_.kt;
+    cg[c].kind = C_.kind;
+    cg[c].a = C_.a;
+    cg[c].dref = C_.dref;
+    cg[c].free_idx = (C_.kind == CK_FREE) ? nfree++ : -1;
+    cg[c].reac_idx = (C_.kind == CK_REAC) ? nreac++ : -1;
+  }
+  std::vector<long> m2m_base(nc * 23, -1), l2l_base(nc * 23, -1), m2l_base(nc * 23, -1);
+  std::vector<SepJob> sep;
+  long off_shift = 0, off_m2l = 0;
+  std::vector<SepJob> sep_m2l;
+  for (int c = 0; c < nc; ++c) {
+    for (int l = 3; l <= maxlev; ++l) {
+      if (!has_level[c][l]) continue;
+      double w = cg[c].h2 / (double)(1 << l);
+      // M2M: child at level l into parent at level l-1 (source k); L2L (target k)
+      m2m_base[c * 23 + l] = off_shift;
+      for (int o = 0; o < 8; ++o) {
+        SepJob j{};
+        for (int a = 0; a < 3; ++a) j.b[a] = (((o >> a) & 1) ? 0.5 : -0.5) * w;
+        j.k = cg[c].ks;
+        j.kind = 1;
+        j.out_off = off_shift + (long)o * PP;
+        sep.push_back(j);
+      }
+      off_shift += 8 * PP;
+      l2l_base[c * 23 + l] = off_shift;
+      for (int o = 0; o < 8; ++o) {
+        SepJob j{};
+        for (int a = 0; a < 3; ++a) j.b[a] = (((o >> a) & 1) ? 0.5 : -0.5) * w;
+        j.k = cg[c].kt;
+        j.kind = 2;
+        j.out_off = off_shift + (long)o * PP;
+        sep.push_back(j);
+      }
+      off_shift += 8 * PP;
+    }
+  }
+  // free-space M2L operators: 343 slots per (component, level >= 2)
+  std::vector<ReacJob> rjobs;
+  std::vector<ExpandJob> expand;
+  long off_radial = 0;
+  double wmin_reac = INFINITY;
+  for (int c = 0; c < nc; ++c) {
+    for (int l = 2; l <= maxlev; ++l) {
+      if (!has_level[c][l]) continue;
+      double w = cg[c].h2 / (double)(1 << l);
+      if (comps[c].kind == CK_FREE) {
+        m2l_base[c * 23 + l] = off_m2l;
+        for (int dz = -3; dz <= 3; ++dz)
+          for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+              int slot = ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
+              if (std::max(abs(dx), std::max(abs(dy), abs(dz))) < 2) continue;
+              SepJob j{};
+              j.b[0] = dx * w; j.b[1] = dy * w; j.b[2] = dz * w;
+              j.k = cg[c].kt;
+              j.kind = 0;
+              j.out_off = off_m2l + slot * PP;
+              sep_m2l.push_back(j);
+            }
+        off_m2l += 343 * PP;
+      } else {
+        wmin_reac = std::min(wmin_reac, w);
+        m2l_base[c * 23 + l] = off_m2l;
+        const Comp& C_ = comps[c];
+        long sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b);   // * Q later
+        for (int jt = 0; jt < 2; ++jt)
+          for (int js = 0; js < 2; ++js) {
+            long radial_of[10];
+            for (int r = 0; r < 10; ++r) radial_of[r] = -1;
+            for (int r = 0; r < 10; ++r) {
+              if (jt == 0 && js == 0 && RHO2[r] < 4) continue;
+              ReacJob j{};
+              j.l = C_.l; j.lp = C_.lp; j.a = C_.a; j.b = C_.b;
+              j.kl = h->k[C_.l]; j.klp = h->k[C_.lp];
+              j.zt = (jt + 0.5) * w;
+              j.zs = (js + 0.5) * w;
+              j.rho = sqrt((double)RHO2[r]) * w;
+              j.phi = 0.0;
+              j.out_off = off_radial;
+              j.sig_off = sig_off;        // completed below
+              j.Q = 0;                    // completed below
+              radial_of[r] = off_radial;
+              off_radial += PP;
+              rjobs.push_back(j);
+            }
+            for (int dy = -3; dy <= 3; ++dy)
+              for (int dx = -3; dx <= 3; ++dx) {
+                int r = rho2_index(dx * dx + dy * dy);
+                if (r < 0 || radial_of[r] < 0) continue;
+                int slot = ((jt * 2 + js) * 7 + (dy + 3)) * 7 + (dx + 3);
+                expand.push_back({radial_of[r], off_m2l + slot * PP, atan2((double)dy, (double)dx)});
+              }
+          }
+        off_m2l += 196 * PP;
+      }
+    }
+  }
+  // make the rule long enough for the reaction operators and near field
+  double tmax = h->rule.ta;
+  if (std::isfinite(wmin_reac)) tmax = std::max(tmax, h->rule.ta + (30.0 + 7.0 * p) / wmin_reac);
+  double gmin = INFINITY, smin = INFINITY;
+  for (int l = 0; l < h->L1; ++l)
+    for (int sd = 0; sd < 2; ++sd) {
+      smin = fmin(smin, gap[(0 * h->L1 + l) * 2 + sd]);
+      gmin = fmin(gmin, gap[(1 * h->L1 + l) * 2 + sd]);
+    }
+  if (h->L1 > 1 && std::isfinite(gmin + smin)) tmax = std::max(tmax, h->rule.ta + 30.0 / (gmin + smin));
+  rule_extend(h, tmax, st);
+  const int Q = h->rule.Q();
+  for (ReacJob& j : rjobs) {
+    j.sig_off *= Q;
+    double H = j.zt + j.zs;
+    j.Q = h->rule.nodes_to(h->rule.ta + (30.0 + 7.0 * p) / H);
+  }
+  h->stats.n_quad_total = Q;
+  // build operators
+  cplx* shift_ops = need<cplx>(ws.m2m_op, std::max<long>(off_shift, 1));
+  cplx* m2l_ops = need<cplx>(ws.m2l_free, std::max<long>(off_m2l, 1));
+  cplx* radial = need<cplx>(ws.m2l_reac, std::max<long>(off_radial, 1));
+  {
+    SepJob* dj = (SepJob*)need<char>(ws.l2l_op, sizeof(SepJob) * std::max<size_t>(1, sep.size() + sep_m2l.size()));
+    std::vector<SepJob> all = sep;
+    size_t n_shift = sep.size();
+    for (SepJob j : sep_m2l) all.push_back(j);
+    FMM_CHECK(cudaMemcpyAsync(dj, all.data(), sizeof(SepJob) * all.size(), cudaMemcpyHostToDevice, st));
+    launch_sep_ops(p, dj, (int)n_shift, h->tab.gaunt.as<double>(), shift_ops, st);
+    launch_sep_ops(p, dj + n_shift, (int)sep_m2l.size(), h->tab.gaunt.as<double>(), m2l_ops, st);
+    FMM_CHECK(cudaGetLastError());
+    if (!rjobs.empty()) {
+      ReacJob* rj = (ReacJob*)need<char>(ws.out_tmp, sizeof(ReacJob) * rjobs.size());
+      FMM_CHECK(cudaMemcpyAsync(rj, rjobs.data(), sizeof(ReacJob) * rjobs.size(), cudaMemcpyHostToDevice, st));
+      launch_reac_T(p, rj, (int)rjobs.size(), h->rule, radial, st);
+      FMM_CHECK(cudaGetLastError());
+      ExpandJob* dex = (ExpandJob*)need<char>(ws.op_tab, sizeof(ExpandJob) * expand.size());
+      FMM_CHECK(cudaMemcpyAsync(dex, expand.data(), sizeof(ExpandJob) * expand.size(), cudaMemcpyHostToDevice, st));
+      launch_phase_expand(p, dex, (int)expand.size(), radial, m2l_ops, st);
+      FMM_CHECK(cudaGetLastError());
+    }
+    FMM_CHECK(cudaStreamSynchronize(st));
+  }
+  h->stats.ms_operators = ms_since(t1);
+  // ---- passes
+  auto t2 = Clock::now();
+  CompGeom* dcg = upload(ws.segl, cg, st);   // segl is free after the tree build
+  long* dm2m = nullptr;
+  {
+    std::vector<long> tabs;
+    tabs.insert(tabs.end(), m2m_base.begin(), m2m_base.end());
+    tabs.insert(tabs.end(), l2l_base.begin(), l2l_base.end());
+    tabs.insert(tabs.end(), m2l_base.begin(), m2l_base.end());
+    dm2m = upload(ws.lvlscan, tabs, st);
+  }
+  BoxGeom B;
+  B.comp = ws.bcomp.as<int>(); B.lev = ws.blevel.as<int>(); B.sb = ws.bsb.as<int>(); B.se = ws.bse.as<int>();
+  B.tb = ws.btb.as<int>(); B.te = ws.bte.as<int>(); B.parent = ws.bparent.as<int>();
+  B.child0 = ws.bchild0.as<int>(); B.nchild = ws.bnchild.as<int>(); B.coord = ws.bcoord.as<int>();
+  cplx* M = need<cplx>(ws.M, (size_t)nb * P);
+  cplx* L = need<cplx>(ws.L, (size_t)nb * P);
+  // schedules
+  std::vector<int> p2m_leaves, l2p_leaves, near_leaves;
+  std::vector<std::vector<int>> m2m_lvl(23), m2l_lvl(23);
+  for (int l = 0; l <= maxlev; ++l)
+    for (int b = lvl[l]; b < lvl[l + 1]; ++b) {
+      bool src_ = bse[b] > bsb[b], tgt_ = bte[b] > btb[b];
+      bool leaf = bnchild[b] == 0;
+      if (src_ && l >= 2) {
+        if (leaf) p2m_leaves.push_back(b);
+        else m2m_lvl[l].push_back(b);
+      }
+      if (tgt_ && l >= 2) m2l_lvl[l].push_back(b);
+      if (tgt_ && leaf) {
+        near_leaves.push_back(b);
+        if (l >= 2) l2p_leaves.push_back(b);
+      }
+    }
+  std::vector<int> sched;
+  auto push = [&](const std::vector<int>& v) { long o = sched.size(); sched.insert(sched.end(), v.begin(), v.end()); return o; };
+  long o_p2m = push(p2m_leaves), o_l2p = push(l2p_leaves), o_near = push(near_leaves);
+  std::vector<long> o_m2m(23), o_m2l(23);
+  for (int l = 0; l <= maxlev; ++l) { o_m2m[l] = push(m2m_lvl[l]); o_m2l[l] = push(m2l_lvl[l]); }
+  int* dsched = upload(ws.lvlcnt, sched, st);
+  int* err = need<int>(ws.flags, 1);
+  FMM_CHECK(cudaMemsetAsync(err, 0, 4, st));
+  // upward pass
+  launch_p2m(p, dsched + o_p2m, (int)p2m_leaves.size(), B, dcg, ws.spos.as<double>(), ws.sq.as<cplx>(), M, st);
+  for (int l = maxlev; l >= 2; --l)
+    launch_m2m(p, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, dm2m, shift_ops, M, st);
+  FMM_CHECK(cudaGetLastError());
+  // downward pass
+  OpIndex OI;
+  OI.m2l_base = dm2m + 2 * nc * 23;
+  OI.l2l_base = dm2m + nc * 23;
+  OI.cgs = dcg;
+  const int* loff = ws.loff.as<int>();
+  for (int l = 2; l <= maxlev; ++l)
+    launch_m2l(p, dsched + o_m2l[l], (int)m2l_lvl[l].size(), l >= 3 ? 1 : 0, B, OI, loff, ws.vi.as<int>(),
+               m2l_ops, shift_ops, M, L, err, st);
+  FMM_CHECK(cudaGetLastError());
+  cplx* phi = need<cplx>(ws.phi, std::max<long>(1, comps.empty() ? 1 : comps.back().to + comps.back().nt));
+  long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;
+  FMM_CHECK(cudaMemsetAsync(phi, 0, sizeof(cplx) * NT, st));
+  launch_l2p(p, dsched + o_l2p, (int)l2p_leaves.size(), B, dcg, ws.tpos.as<double>(), L, phi, st);
+  // near field
+  cplx* coef = rule_coef(h, st);
+  std::vector<NearComp> ncs(nc);
+  for (int c = 0; c < nc; ++c) {
+    const Comp& C_ = comps[c];
+    ncs[c].kind = C_.kind; ncs[c].l = C_.l; ncs[c].lp = C_.lp; ncs[c].a = C_.a; ncs[c].b = C_.b;
+    ncs[c].k = C_.kt;
+    ncs[c].dref = C_.dref;
+    ncs[c].coef_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * Q;
+  }
+  NearComp* dnc = upload(ws.segs, ncs, st);
+  NearBoxes NB;
+  NB.comp = B.comp; NB.lev = B.lev; NB.sb = B.sb; NB.se = B.se; NB.tb = B.tb; NB.te = B.te; NB.parent = B.parent;
+  NB.uo = loff + (nb + 1); NB.ui = ws.ui.as<int>();
+  NB.wo = loff + 2 * (nb + 1); NB.wi = ws.wi.as<int>();
+  NB.xo = loff + 3 * (nb + 1); NB.xi = ws.xi.as<int>();
+  launch_near(dsched + o_near, (int)near_leaves.size(), NB, dnc, make_rule_view(h->rule, coef),
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, st);
+  FMM_CHECK(cudaGetLastError());
+  // sum of the components in their fixed order
+  for (int c = 0; c < nc; ++c)
+    launch_scatter_add(comps[c].nt, ws.tidx.as<int>() + comps[c].to, phi + comps[c].to, out, st);
+  if (h->flags & FMM_NORM_PAPER) launch_norm_paper(nt, tgt, medium_of(h), out, st);
+  FMM_CHECK(cudaGetLastError());
+  int herr = 0;
+  FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaStreamSynchronize(st));
+  if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair outside the interface band");
+  h->stats.ms_eval = ms_since(t2);
+}
+
+extern "C" int fmm_layered_eval(fmm_layered_t* h, long ns, const double* src, const double* q, long nt,
+                                const double* tgt, double* out, void* stream) {
+  if (!h) return FMM_ERR_ARG;
+  h->err.clear();
+  if (ns < 0 || nt < 0 || (ns && (!src || !q)) || (nt && (!tgt || !out))) {
+    h->err = "invalid argument";
+    return FMM_ERR_ARG;
+  }
+  try {
+    eval_impl(h, ns, src, q, nt, tgt, out, (cudaStream_t)stream);
+  } catch (FmmError& e) {
+    h->err = e.msg;
+    return e.code;
+  }
+  h->nsrc_last = ns;
+  h->ntgt_last = nt;
+  return FMM_OK;
+}
+
+extern "C" int fmm_layered_eval_host(fmm_layered_t* h, long ns, const double* src, const double* q, long nt,
+                                     const double* tgt, double* out, void* stream) {
+  if (!h) return FMM_ERR_ARG;
+  h->err.clear();
+  if (ns < 0 || nt < 0 || (ns && (!src || !q)) || (nt && (!tgt || !out))) {
+    h->err = "invalid argument";
+    return FMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf bs, bq, bt, bo;
+  int rc = FMM_OK;
+  try {
+    double* ds = need<double>(bs, 3 * ns);
+    double* dq = need<double>(bq, 2 * ns);
+    double* dt = need<double>(bt, 3 * nt);
+    double* dout = need<double>(bo, 2 * nt);
+    if (ns) FMM_CHECK(cudaMemcpyAsync(ds, src, sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, st));
+    if (ns) FMM_CHECK(cudaMemcpyAsync(dq, q, sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, st));
+    if (nt) FMM_CHECK(cudaMemcpyAsync(dt, tgt, sizeof(double) * 3 * nt, cudaMemcpyHostToDevice, st));
+    eval_impl(h, ns, ds, dq, nt, dt, dout, st);
+    if (nt) FMM_CHECK(cudaMemcpyAsync(out, dout, sizeof(double) * 2 * nt, cudaMemcpyDeviceToHost, st));
+    FMM_CHECK(cudaStreamSynchronize(st));
+  } catch (FmmError& e) {
+    h->err = e.msg;
+    rc = e.code;
+  }
+  bs.release(); bq.release(); bt.release(); bo.release();
+  return rc;
+}
+
+// ---------------------------------------------------------------- export
+extern "C" int fmm_layered_num_components(const fmm_layered_t* h) {
+  return h ? (int)h->comps.size() : FMM_ERR_ARG;
+}
+
+extern "C" int fmm_layered_component_info(const fmm_layered_t* hc, int c, long long* info, double* root) {
+  fmm_layered* h = const_cast<fmm_layered*>(hc);
+  if (!h || c < 0 || c >= (int)h->comps.size() || !info || !root) return FMM_ERR_ARG;
+  const Comp& C_ = h->comps[c];
+  std::vector<int> comp(h->nboxes);
+  cudaMemcpy(comp.data(), h->ws.bcomp.ptr, 4 * h->nboxes, cudaMemcpyDeviceToHost);
+  std::vector<int> lev(h->nboxes);
+  cudaMemcpy(lev.data(), h->ws.blevel.ptr, 4 * h->nboxes, cudaMemcpyDeviceToHost);
+  long nbc = 0;
+  int nlev = 0;
+  for (int b = 0; b < h->nboxes; ++b)
+    if (comp[b] == c) { ++nbc; nlev = std::max(nlev, lev[b] + 1); }
+  info[0] = C_.kind; info[1] = C_.l; info[2] = C_.lp; info[3] = C_.a; info[4] = C_.b;
+  info[5] = C_.ns; info[6] = C_.nt; info[7] = nbc; info[8] = nlev; info[9] = 0;
+  root[0] = C_.c[0]; root[1] = C_.c[1]; root[2] = C_.c[2]; root[3] = C_.h;
+  return FMM_OK;
+}
+
+extern "C" int fmm_layered_tree_export(const fmm_layered_t* hc, int c, int* level, long long* prefix,
+                                       int* src_begin, int* src_end, int* tgt_begin, int* tgt_end, int* parent,
+                                       int* src_perm, int* tgt_perm, int* list_off, int* v_idx, int* u_idx,
+                                       int* w_idx, int* x_idx) {
+  fmm_layered* h = const_cast<fmm_layered*>(hc);
+  if (!h || c < 0 || c >= (int)h->comps.size()) return FMM_ERR_ARG;
+  const Comp& C_ = h->comps[c];
+  std::vector<int> comp, lev, sb, se, tb, te, par;
+  std::vector<unsigned long long> pre;
+  tree_host_copy(h, comp, lev, pre, sb, se, tb, te, par);
+  int nb = h->nboxes;
+  std::vector<int> local(nb, -1);
+  std::vector<int> glob;
+  for (int b = 0; b < nb; ++b)
+    if (comp[b] == c) { local[b] = (int)glob.size(); glob.push_back(b); }
+  int nbc = (int)glob.size();
+  for (int i = 0; i < nbc; ++i) {
+    int b = glob[i];
+    if (level) level[i] = lev[b];
+    if (prefix) prefix[i] = (long long)pre[b];
+    if (src_begin) src_begin[i] = sb[b] - (int)C_.so;
+    if (src_end) src_end[i] = se[b] - (int)C_.so;
+    if (tgt_begin) tgt_begin[i] = tb[b] - (int)C_.to;
+    if (tgt_end) tgt_end[i] = te[b] - (int)C_.to;
+    if (parent) parent[i] = par[b] < 0 ? -1 : local[par[b]];
+  }
+  if (src_perm && C_.ns)
+    cudaMemcpy(src_perm, h->ws.slocal.as<int>() + C_.so, 4 * C_.ns, cudaMemcpyDeviceToHost);
+  if (tgt_perm && C_.nt)
+    cudaMemcpy(tgt_perm, h->ws.tlocal.as<int>() + C_.to, 4 * C_.nt, cudaMemcpyDeviceToHost);
+  if (list_off) {
+    std::vector<int> off(4 * (size_t)(nb + 1));
+    cudaMemcpy(off.data(), h->ws.loff.ptr, 4 * off.size(), cudaMemcpyDeviceToHost);
+    int* idxs[4] = {v_idx, u_idx, w_idx, x_idx};
+    DevBuf* bufs[4] = {&h->ws.vi, &h->ws.ui, &h->ws.wi, &h->ws.xi};
+    for (int k = 0; k < 4; ++k) {
+      const int* o = off.data() + (size_t)k * (nb + 1);
+      std::vector<int> all(o[nb]);
+      if (idxs[k] && o[nb]) cudaMemcpy(all.data(), bufs[k]->ptr, 4 * (size_t)o[nb], cudaMemcpyDeviceToHost);
+      int* lo = list_off + (size_t)k * (nbc + 1);
+      lo[0] = 0;
+      for (int i = 0; i < nbc; ++i) {
+        int b = glob[i];
+        int n = o[b + 1] - o[b];
+        lo[i + 1] = lo[i] + n;
+        if (idxs[k])
+          for (int e = 0; e < n; ++e) idxs[k][lo[i] + e] = local[all[o[b] + e]];
+      }
+    }
+  }
+  return FMM_OK;
+}

@@ -1,0 +1,265 @@
+// Near-field (direct) interactions and the all-pairs direct sum.
+//
+// Free space: e^{ik r} / (4 pi r), skipped for bitwise-identical points.
+// Reaction component (l, l', a, b) between a target at height zt = |z - d| on
+// its side of the reference interface d and an image at depth zs = |z* - d|:
+//   u~ = (i/4pi) int k_rho J_0(k_rho rho) e^{i k_lz zt + i k_l'z zs} sigma^{ab}/k_lz dk_rho
+// (eq. generalcomponentsimag after the alpha integral).  The integral is taken
+// on the rule's contour up to t_max = ta + 30 / (zt + zs), where the
+// integrand has decayed below e^{-30} of its scale; on the real tail every
+// factor is real and the integrand is evaluated in real arithmetic.
+#include <cmath>
+#include <vector>
+
+#include "fmm_internal.h"
+
+#define TAIL_DECAY 30.0
+
+
+
+__device__ inline int rule_nodes(const RuleView& R, double tmax) {
+  if (tmax <= R.ta) return R.n_near;
+  int np = (int)ceil((tmax - R.ta) / R.panel);
+  if (np > R.n_panels) np = R.n_panels;
+  return R.n_near + R.per_panel * np;
+}
+
+// J_0(z), complex z: power series for |z| <= 8, Miller's recurrence beyond.
+__device__ inline cplx j0c(cplx z) {
+  if (cabs2(z) <= 64.0) return j0_series(z);
+  cplx J[1];
+  besselJ_all(0, z, J);
+  return J[0];
+}
+
+// One reaction pair on the rule (coef already holds sigma for the component).
+__device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coef, const cplx* __restrict__ kzl,
+                                 const cplx* __restrict__ kzp, double rho, double zt, double zs) {
+  int nq = rule_nodes(R, R.ta + TAIL_DECAY / (zt + zs));
+  cplx acc = C(0, 0);
+  for (int q = 0; q < R.n_near; ++q) {
+    cplx e = cexp_(cadd(cmul(C(0, zt), kzl[q]), cmul(C(0, zs), kzp[q])));
+    cplx J = j0c(cscale(R.kr[q], rho));
+    cfma(acc, cmul(J, e), coef[q]);
+  }
+  double tail = 0.0;
+  for (int q = R.n_near; q < nq; ++q) {
+    double t = R.kr[q].x;
+    // k_z = i kappa on the real axis beyond every k_j
+    double e = exp(-(kzl[q].y * zt + kzp[q].y * zs));
+    tail += coef[q].x * j0(t * rho) * e;
+  }
+  return cadd(acc, C(tail, 0.0));
+}
+
+
+
+
+
+#define NEAR_CHUNK 128
+__global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearComp* __restrict__ ncs,
+                       RuleView R, const double* __restrict__ spos, const cplx* __restrict__ sq,
+                       const double* __restrict__ tpos, cplx* __restrict__ phi) {
+  int T = leaves[blockIdx.x];
+  const NearComp nc = ncs[B.comp[T]];
+  __shared__ double sx[NEAR_CHUNK], sy[NEAR_CHUNK], sz[NEAR_CHUNK];
+  __shared__ cplx sqs[NEAR_CHUNK];
+  const cplx* coef = R.coef + nc.coef_off;
+  const cplx* kzl = R.kz + (long)nc.l * R.Q;
+  const cplx* kzp = R.kz + (long)nc.lp * R.Q;
+  for (int t0 = B.tb[T]; t0 < B.te[T]; t0 += blockDim.x) {
+    int t = t0 + threadIdx.x;
+    bool act = t < B.te[T];
+    double x = 0, y = 0, z = 0;
+    if (act) { x = tpos[3 * t]; y = tpos[3 * t + 1]; z = tpos[3 * t + 2]; }
+    cplx acc = C(0, 0);
+    // list walk: U(T), W(T), then X(A) for A = T and its ancestors
+    int A = T;
+    int phase = 0;   // 0: U, 1: W, 2: X of A
+    int e = B.uo[T], e_end = B.uo[T + 1];
+    while (true) {
+      while (e >= e_end) {
+        if (phase == 0) { phase = 1; e = B.wo[T]; e_end = B.wo[T + 1]; }
+        else if (phase == 1) { phase = 2; A = T; e = B.xo[A]; e_end = B.xo[A + 1]; }
+        else {
+          A = B.parent[A];
+          if (A < 0) break;
+          e = B.xo[A]; e_end = B.xo[A + 1];
+        }
+      }
+      if (phase == 2 && A < 0) break;
+      int S = (phase == 0) ? B.ui[e] : (phase == 1) ? B.wi[e] : B.xi[e];
+      ++e;
+      for (int s0 = B.sb[S]; s0 < B.se[S]; s0 += NEAR_CHUNK) {
+        int ns = min(NEAR_CHUNK, B.se[S] - s0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+          sx[k] = spos[3 * (s0 + k)]; sy[k] = spos[3 * (s0 + k) + 1]; sz[k] = spos[3 * (s0 + k) + 2];
+          sqs[k] = sq[s0 + k];
+        }
+        __syncthreads();
+        if (act) {
+          if (nc.kind == CK_FREE) {
+            for (int k = 0; k < ns; ++k) {
+              double dx = x - sx[k], dy = y - sy[k], dz = z - sz[k];
+              if (dx == 0.0 && dy == 0.0 && dz == 0.0) continue;
+              double r = sqrt(dx * dx + dy * dy + dz * dz);
+              double s, c;
+              sincos(nc.k * r, &s, &c);
+              double f = 1.0 / (4.0 * FMM_PI * r);
+              cfma(acc, C(c * f, s * f), sqs[k]);
+            }
+          } else {
+            double zt = fabs(z - nc.dref);
+            for (int k = 0; k < ns; ++k) {
+              double dx = x - sx[k], dy = y - sy[k];
+              double rho = sqrt(dx * dx + dy * dy);
+              double zs = fabs(sz[k] - nc.dref);
+              cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs), sqs[k]);
+            }
+          }
+        }
+      }
+    }
+    if (act) phi[t] = cadd(phi[t], acc);
+  }
+}
+
+// All-pairs direct sum on the GPU: one thread per target, sources streamed
+// through shared memory.  Reaction part: all (a, b) of the layer pair.
+
+
+__global__ void k_direct(long nt, const double* __restrict__ tgt, long ns, const double* __restrict__ src,
+                         const double* __restrict__ q, DirectMedium md, RuleView R,
+                         const cplx* __restrict__ coef_all, double* __restrict__ out) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  __shared__ double sx[NEAR_CHUNK], sy[NEAR_CHUNK], sz[NEAR_CHUNK];
+  __shared__ cplx sqs[NEAR_CHUNK];
+  __shared__ int sl[NEAR_CHUNK];
+  bool act = t < nt;
+  double x = 0, y = 0, z = 0;
+  int lt = 0;
+  if (act) {
+    x = tgt[3 * t]; y = tgt[3 * t + 1]; z = tgt[3 * t + 2];
+    for (int j = 0; j < md.L1 - 1; ++j) if (z < md.d[j]) ++lt;
+  }
+  cplx acc = C(0, 0);
+  for (long s0 = 0; s0 < ns; s0 += NEAR_CHUNK) {
+    int nsb = (int)min((long)NEAR_CHUNK, ns - s0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
+      long s = s0 + k;
+      sx[k] = src[3 * s]; sy[k] = src[3 * s + 1]; sz[k] = src[3 * s + 2];
+      sqs[k] = C(q[2 * s], q[2 * s + 1]);
+      int l = 0;
+      for (int j = 0; j < md.L1 - 1; ++j) if (sz[k] < md.d[j]) ++l;
+      sl[k] = l;
+    }
+    __syncthreads();
+    if (!act) continue;
+    for (int k = 0; k < nsb; ++k) {
+      int ls = sl[k];
+      double dx = x - sx[k], dy = y - sy[k], dz = z - sz[k];
+      if (ls == lt && !(dx == 0.0 && dy == 0.0 && dz == 0.0)) {
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double s, c;
+        sincos(md.k[lt] * r, &s, &c);
+        double f = 1.0 / (4.0 * FMM_PI * r);
+        cfma(acc, C(c * f, s * f), sqs[k]);
+      }
+      if (md.L1 == 1) continue;
+      double rho = sqrt(dx * dx + dy * dy);
+      const cplx* kzl = R.kz + (long)lt * R.Q;
+      const cplx* kzp = R.kz + (long)ls * R.Q;
+      for (int a = 0; a < 2; ++a) {
+        if (a == AR_UP ? !(lt < md.L1 - 1) : !(lt > 0)) continue;
+        double zt = (a == AR_UP) ? (z - md.d[lt]) : (md.d[lt - 1] - z);
+        for (int b = 0; b < 2; ++b) {
+          if (b == AR_UP ? !(ls < md.L1 - 1) : !(ls > 0)) continue;
+          double zs = (b == AR_UP) ? (sz[k] - md.d[ls]) : (md.d[ls - 1] - sz[k]);
+          const cplx* coef = coef_all + ((((long)lt * md.L1 + ls) * 2 + a) * 2 + b) * R.Q;
+          cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs), sqs[k]);
+        }
+      }
+    }
+  }
+  if (act) {
+    out[2 * t] = acc.x;
+    out[2 * t + 1] = acc.y;
+  }
+}
+
+// coef[(l,l',a,b)][q] = (i / 4 pi) w k_rho sigma^{ab}_{l l'} / k_lz
+__global__ void k_coef(int L1, int Q, const cplx* __restrict__ kr, const cplx* __restrict__ w,
+                       const cplx* __restrict__ kz, const cplx* __restrict__ sigma, cplx* __restrict__ coef) {
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long total = (long)L1 * L1 * 4 * Q;
+  if (e >= total) return;
+  int q = e % Q;
+  long combo = e / Q;
+  int l = (int)(combo / (L1 * 4));
+  cplx v = cdiv(cmul(cmul(w[q], kr[q]), sigma[e]), kz[(long)l * Q + q]);
+  coef[e] = cmul(C(0.0, 1.0 / (4.0 * FMM_PI)), v);
+}
+
+// out[tidx[i]] += phi[i] for one component's target segment
+__global__ void k_scatter_add(long n, const int* __restrict__ tidx, const cplx* __restrict__ phi, double* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long g = tidx[i];
+  out[2 * g] += phi[i].x;
+  out[2 * g + 1] += phi[i].y;
+}
+
+// paper normalization: multiply by 4 pi / (i k_l) for targets in layer l
+__global__ void k_norm_paper(long n, const double* __restrict__ tgt, DirectMedium md, double* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double z = tgt[3 * i + 2];
+  int l = 0;
+  for (int j = 0; j < md.L1 - 1; ++j) if (z < md.d[j]) ++l;
+  double f = 4.0 * FMM_PI / md.k[l];
+  double re = out[2 * i], im = out[2 * i + 1];
+  // (re + i im) * f / i = f * (im - i re)
+  out[2 * i] = f * im;
+  out[2 * i + 1] = -f * re;
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st) {
+  long total = (long)L1 * L1 * 4 * R.Q();
+  k_coef<<<(total + 255) / 256, 256, 0, st>>>(L1, R.Q(), R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(),
+                                              R.sigma.as<cplx>(), coef);
+}
+
+RuleView make_rule_view(const Rule& R, const cplx* coef) {
+  RuleView v;
+  v.kr = R.kr.as<cplx>();
+  v.coef = coef;
+  v.kz = R.kz.as<cplx>();
+  v.Q = R.Q();
+  v.n_near = R.n_near;
+  v.per_panel = R.per_panel;
+  v.n_panels = R.n_tail_panels;
+  v.ta = R.ta;
+  v.panel = R.panel;
+  return v;
+}
+
+void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
+                 const cplx* sq, const double* tpos, cplx* phi, cudaStream_t st) {
+  if (n) k_near<<<n, 64, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi);
+}
+
+void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
+                   RuleView R, const cplx* coef_all, double* out, cudaStream_t st) {
+  if (nt) k_direct<<<(nt + 63) / 64, 64, 0, st>>>(nt, tgt, ns, src, q, md, R, coef_all, out);
+}
+
+void launch_scatter_add(long n, const int* tidx, const cplx* phi, double* out, cudaStream_t st) {
+  if (n) k_scatter_add<<<(n + 255) / 256, 256, 0, st>>>(n, tidx, phi, out);
+}
+
+void launch_norm_paper(long n, const double* tgt, DirectMedium md, double* out, cudaStream_t st) {
+  if (n) k_norm_paper<<<(n + 255) / 256, 256, 0, st>>>(n, tgt, md, out);
+}
