@@ -1,0 +1,257 @@
+"""Benchmark of the layered-media Helmholtz FMM evaluation on GB300.
+
+Default workload: the three-layer medium (interfaces z = 0, -1.2; k = 0.8,
+1.2, 1.6; eps = 1, 2, 3) with N = 32,768 particles split evenly over the cubes
+[-1,1]^2 x {[0.1,1.1], [-1.1,-0.1], [-2.3,-1.3]}, charges U[0,1], targets =
+sources, p = 8, leaf 64, FP64 throughout.  One step = one full evaluation
+(classification, trees, lists, translation operators, upward and downward
+passes, near field, sum), inputs resident in device memory.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank evaluates its own independent problem of the
+same size (weak scaling, no data-path collective); the barrier and the
+max-over-ranks time use torch.distributed.  --impl reference times the CPU
+oracle (the only reference implementation this project has) on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="three-layer N=32768 p=8 leaf=64", n=32768, p=8, leaf=64)
+METRIC = "FMM particles/sec at rel L2 err 1e-6 (FP64)"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(path, dev):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def _clock_summary(path):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def _algorithmic(stats, p, n):
+    """Algorithmic FP64 flops of each stage (conventions stated in the design doc)."""
+    P2 = (p + 1) ** 2
+    P4 = P2 * P2
+    return {
+        "near_reac": 60.0 * stats["n_reac_nodes"],
+        "near_free": 30.0 * stats["n_free_pairs"],
+        "m2l": 8.0 * P4 * stats["n_v_pairs"],
+        "operators": 8.0 * P4 * stats["n_reac_T_nodes"],
+    }
+
+
+def cpu_oracle_sample(n_sample, seed=0):
+    """Time the oracle FMM (as it stands) on n_sample particles of the same
+    workload distribution, single-threaded, in a child process."""
+    code = (
+        "import sys,time,json;sys.path.insert(0,%r);"
+        "from oracle.media import Medium;from oracle import fmm;"
+        "from paper_1902_05132_gb300 import workloads as wl;"
+        "w=wl.three_layer(n=%d,seed=%d,p=%d,leaf=%d);m=Medium(w['k'],w['d'],w['eps']);"
+        "fmm._sep_index(%d);t=time.perf_counter();"
+        "fmm.FMM(m,%d,%d).evaluate(w['src'],w['q'],w['tgt']);"
+        "print(json.dumps({'seconds':time.perf_counter()-t}))"
+    ) % (ROOT, n_sample, seed, WORKLOAD["p"], WORKLOAD["leaf"], WORKLOAD["p"], WORKLOAD["p"], WORKLOAD["leaf"])
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    return n_sample / sec, sec
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    n_sample = 300
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n_sample)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s = cpu_oracle_sample(n_sample)
+        vals.append(v)
+        secs.append(s)
+    value = statistics.median(vals)
+    sample = f"oracle FMM on {n_sample} particles of the three-layer workload (same medium, p, leaf; all targets)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample_particles": n_sample},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_1902_05132_gb300 as pkg
+    from paper_1902_05132_gb300 import _build, workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    w = workloads.three_layer(n=WORKLOAD["n"], seed=rank, p=WORKLOAD["p"], leaf=WORKLOAD["leaf"])
+    solver = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
+    src = torch.tensor(w["src"], device=dev)
+    q = torch.tensor(w["q"], device=dev)
+    tgt = torch.tensor(w["tgt"], device=dev)
+    out = torch.empty(len(w["tgt"]), dtype=torch.complex128, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        solver.eval(src, q, tgt, out=out)
+    torch.cuda.synchronize()
+    clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
+    os.makedirs(os.path.dirname(clock_path), exist_ok=True)
+    sampler = _clock_sampler(clock_path, local)
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, stage = [], []
+    launches = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # evict the L2 between steps
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.eval(src, q, tgt, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st = solver.stats()
+        stage.append(st)
+        launches += st["n_launches"]
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    total_ms = sum(ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    n = len(w["tgt"])
+    value = ws * n / (ms_per_step * 1e-3)
+
+    # end to end through the public API with host buffers (pinned)
+    hs = torch.tensor(w["src"]).pin_memory().numpy()
+    hq = torch.tensor(w["q"]).pin_memory().numpy()
+    ht = torch.tensor(w["tgt"]).pin_memory().numpy()
+    solver.eval_host(hs, hq, ht)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = solver.eval_host(hs, hq, ht)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = ws * n / (statistics.mean(e2e_ms) * 1e-3)
+    h2d = hs.nbytes + hq.nbytes + ht.nbytes
+    d2h = res.nbytes
+
+    # roofline of the dominant stage (FP64 pipe, peak measured on this GPU now)
+    keys = ["tree", "operators", "upward", "m2l", "l2p", "near_free", "near_reac", "sum"]
+    mean_stage = {k: statistics.mean(s["gpu_ms_" + k] for s in stage) for k in keys}
+    flops = _algorithmic(stage[-1], w["p"], n)
+    dominant = max((k for k in flops), key=lambda k: mean_stage[k])
+    peak = pkg.measure_fp64_peak() / 1e3
+    achieved = flops[dominant] / (mean_stage[dominant] * 1e-3) / 1e12
+    result = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "medium": "3 layers, d=(0,-1.2), k=(0.8,1.2,1.6), eps=(1,2,3)",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"independent problem per GPU x{ws}"},
+        "clocks": _clock_summary(clock_path),
+        "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FP64 FMA throughput measured on this GPU by the library's probe"},
+        "stage_ms": mean_stage,
+        "counts": {k: stage[-1][k] for k in ("n_components", "n_boxes", "n_v_pairs", "n_free_pairs",
+                                             "n_reac_pairs", "n_reac_nodes", "n_reac_classes", "n_reac_T_nodes")},
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        n_sample = 300
+        v, sec = cpu_oracle_sample(n_sample)
+        result["cpu_baseline"] = {"value": v, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"oracle FMM on {n_sample} particles of the same workload "
+                                            f"distribution (all targets), {sec:.1f} s single-threaded"}
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -64,6 +64,20 @@ typedef struct {
                               levels and lists (host wall clock, synchronous) */
   double ms_operators;     /* translation operators                          */
   double ms_eval;          /* upward, downward, near field and sum           */
+  /* device time of each stage of the last evaluation (CUDA events on the
+     evaluation's stream) */
+  double gpu_ms_tree, gpu_ms_operators, gpu_ms_upward, gpu_ms_m2l, gpu_ms_l2p,
+         gpu_ms_near_free, gpu_ms_near_reac, gpu_ms_sum, gpu_ms_total;
+  long   n_free_pairs;     /* free-space near-field pairs evaluated          */
+  long   n_reac_pairs;     /* reaction near-field pairs evaluated            */
+  long   n_reac_nodes;     /* quadrature nodes summed over reaction pairs    */
+  long   n_reac_tail_nodes;/* ... of which on the real-axis tail             */
+  long   n_reac_classes;   /* reaction M2L radial integrals computed         */
+  long   n_free_ops;       /* free-space translation operators built         */
+  long   n_reac_T_nodes;   /* quadrature nodes summed over those integrals   */
+  long   n_launches;       /* kernels of this library launched by the last
+                              evaluation (launches inside CUB's sort and scan
+                              calls not included)                            */
 } fmm_stats_t;
 
 /*
@@ -73,7 +87,7 @@ typedef struct {
  *   interfaces  [L] d_0 > d_1 > ... (host; NULL when L = 0)
  *   eps         [L+1] material coefficients > 0 in the transmission
  *               condition [eps du/dz] = 0 (host; NULL means all 1)
- *   p           expansion order, 1 <= p <= 20 (terms n = 0..p)
+ *   p           expansion order, 1 <= p <= 16 (terms n = 0..p)
  *   leaf        maximum number of sources or targets in a leaf box, >= 1
  *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER
  *   out         receives the handle (NULL on failure)
@@ -123,6 +137,13 @@ int fmm_layered_eval_host(fmm_layered_t* h, long n_src, const double* src_xyz,
 int fmm_layered_direct(fmm_layered_t* h, long n_src, const double* src_xyz,
                        const double* charges, long n_tgt, const double* tgt_xyz,
                        double* out, void* stream);
+
+/*
+ * Throughput of dependent FP64 fused multiply-adds on the current device
+ * (GFLOP/s, 2 flops per FMA), measured by a short kernel; the denominator of
+ * the FP64 roofline.  Returns FMM_OK and writes *gflops.
+ */
+int fmm_layered_measure_fp64_peak(double* gflops);
 
 /* Statistics of the last create/evaluation. */
 int fmm_layered_stats(const fmm_layered_t* h, fmm_stats_t* stats);

@@ -594,6 +594,16 @@ class FMM:
             for S in V.get(b, []):
                 acc += self._m2l(comp, tree, b, S, cache) @ M[S]
             Lx[b] = acc
+        rule = None
+        if comp.kind == "reac":
+            # one rule for the component: smallest vertical gap and largest
+            # lateral distance of any target/image pair
+            dref = med.d[comp.l] if comp.a == UP else med.d[comp.l - 1]
+            H = float(np.min(np.abs(tpos[:, 2] - dref)) + np.min(np.abs(spos[:, 2] - dref)))
+            rho = 2.0 * math.sqrt(2.0) * tree.h
+            kr, w, ne = oracle_rule(med, H, rho)
+            kz = med.kz(kr)
+            rule = (kr, w, ne, kz, med.sigma(kr, comp.l, comp.lp)[(comp.a, comp.b)])
         res = np.zeros(len(T_sorted), dtype=complex)
         for b in range(nb):
             if not need[b]:
@@ -604,10 +614,10 @@ class FMM:
                 res[idx] += l2p(p, kt, tree.center(b), T_sorted[idx], Lx[b])
                 for S in U.get(b, []) + W.get(b, []):
                     s0, s1 = tree.src_begin[S], tree.src_end[S]
-                    res[idx] += self._direct(comp, T_sorted[idx], S_sorted[s0:s1], q_sorted[s0:s1])
+                    res[idx] += self._direct(comp, T_sorted[idx], S_sorted[s0:s1], q_sorted[s0:s1], rule)
             for S in X.get(b, []):
                 s0, s1 = tree.src_begin[S], tree.src_end[S]
-                res[idx] += self._direct(comp, T_sorted[idx], S_sorted[s0:s1], q_sorted[s0:s1])
+                res[idx] += self._direct(comp, T_sorted[idx], S_sorted[s0:s1], q_sorted[s0:s1], rule)
         out = np.zeros(len(tpos), dtype=complex)
         out[tree.tperm] = res
         return out
@@ -635,7 +645,7 @@ class FMM:
             cache[key] = cache[rkey] * reaction_T_phase(p, phi)
         return cache[key]
 
-    def _direct(self, comp, tpos, spos, q):
+    def _direct(self, comp, tpos, spos, q, rule=None):
         med = self.medium
         if len(tpos) == 0 or len(spos) == 0:
             return np.zeros(len(tpos), complex)
@@ -648,13 +658,7 @@ class FMM:
             G = np.where(same, 0.0, np.exp(1j * k * Rs) / (FOUR_PI * Rs))
             return G @ q
         l, lp, a = comp.l, comp.lp, comp.a
-        dref = med.d[l] if a == UP else med.d[l - 1]
-        H = float(np.min(np.abs(tpos[:, 2] - dref)) + np.min(np.abs(spos[:, 2] - dref)))
-        rho = float(np.max(np.hypot(tpos[:, None, 0] - spos[None, :, 0],
-                                    tpos[:, None, 1] - spos[None, :, 1])))
-        kr, w, ne = oracle_rule(med, H, max(rho, 1e-3))
-        kz = med.kz(kr)
-        sig = med.sigma(kr, l, lp)[(a, comp.b)]
+        kr, w, ne, kz, sig = rule
         f = w * kr * sig / kz[l]
         out = np.zeros(len(tpos), complex)
         for i in range(len(tpos)):

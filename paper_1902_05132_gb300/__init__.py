@@ -33,12 +33,22 @@ class Stats(ctypes.Structure):
     _fields_ = [("n_components", ctypes.c_int), ("n_boxes", ctypes.c_int), ("max_level", ctypes.c_int),
                 ("n_v_pairs", ctypes.c_long), ("n_u_pairs", ctypes.c_long), ("n_quad_near", ctypes.c_int),
                 ("n_quad_total", ctypes.c_int), ("ms_setup", ctypes.c_double), ("ms_tree", ctypes.c_double),
-                ("ms_operators", ctypes.c_double), ("ms_eval", ctypes.c_double)]
+                ("ms_operators", ctypes.c_double), ("ms_eval", ctypes.c_double),
+                ("gpu_ms_tree", ctypes.c_double), ("gpu_ms_operators", ctypes.c_double),
+                ("gpu_ms_upward", ctypes.c_double), ("gpu_ms_m2l", ctypes.c_double),
+                ("gpu_ms_l2p", ctypes.c_double), ("gpu_ms_near_free", ctypes.c_double),
+                ("gpu_ms_near_reac", ctypes.c_double), ("gpu_ms_sum", ctypes.c_double),
+                ("gpu_ms_total", ctypes.c_double), ("n_free_pairs", ctypes.c_long),
+                ("n_reac_pairs", ctypes.c_long), ("n_reac_nodes", ctypes.c_long),
+                ("n_reac_tail_nodes", ctypes.c_long), ("n_reac_classes", ctypes.c_long),
+                ("n_free_ops", ctypes.c_long), ("n_reac_T_nodes", ctypes.c_long),
+                ("n_launches", ctypes.c_long)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
             "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
-            "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export"]
+            "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
+            "fmm_layered_measure_fp64_peak"]
 
 _lib = None
 
@@ -70,6 +80,8 @@ def lib():
     L.fmm_layered_component_info.restype = i
     L.fmm_layered_tree_export.argtypes = [v, i] + [d] * 14
     L.fmm_layered_tree_export.restype = i
+    L.fmm_layered_measure_fp64_peak.argtypes = [d]
+    L.fmm_layered_measure_fp64_peak.restype = i
     _lib = L
     return L
 
@@ -189,3 +201,12 @@ class LayeredFMM:
             out.append(dict(kind=kind, l=l, lp=lp, a=a, b=b, ns=ns, nt=nt, root=root, prefix=prefix.view(np.uint64),
                             sperm=sperm[:ns], tperm=tperm[:nt], lists=lists, **arr))
         return out
+
+
+def measure_fp64_peak():
+    """Dependent-FMA FP64 throughput of the current device, GFLOP/s."""
+    v = ctypes.c_double()
+    rc = lib().fmm_layered_measure_fp64_peak(ctypes.byref(v))
+    if rc != 0:
+        raise FmmError(rc, "peak measurement failed")
+    return v.value

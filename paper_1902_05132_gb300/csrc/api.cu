@@ -26,7 +26,8 @@ void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs,
 void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st);
 RuleView make_rule_view(const Rule& R, const cplx* coef);
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
-                 const cplx* sq, const double* tpos, cplx* phi, cudaStream_t st);
+                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st);
+double measure_fp64_peak_impl();
 void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
                    RuleView R, const cplx* coef_all, double* out, cudaStream_t st);
 void launch_scatter_add(long n, const int* tidx, const cplx* phi, double* out, cudaStream_t st);
@@ -38,6 +39,7 @@ void tree_host_copy(fmm_layered* h, std::vector<int>& comp, std::vector<int>& le
                     std::vector<int>& tb, std::vector<int>& te, std::vector<int>& parent);
 
 static thread_local std::string g_create_err;
+long g_fmm_launches = 0;
 
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t0) {
@@ -212,6 +214,19 @@ static int rho2_index(int r2) {
   return -1;
 }
 
+struct StageEvents {
+  cudaEvent_t ev[10];
+  int n = 0;
+  StageEvents() { for (auto& e : ev) cudaEventCreate(&e); }
+  ~StageEvents() { for (auto& e : ev) cudaEventDestroy(e); }
+  void mark(int i, cudaStream_t st) { cudaEventRecord(ev[i], st); }
+  double ms(int a, int b) {
+    float v = 0;
+    cudaEventElapsedTime(&v, ev[a], ev[b]);
+    return v;
+  }
+};
+
 static void eval_impl(fmm_layered* h, long ns, const double* src, const double* q, long nt, const double* tgt,
                       double* out, cudaStream_t st) {
   Workspace& ws = h->ws;
@@ -219,6 +234,9 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   const long PP = (long)P * P;
   FMM_CHECK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * nt, st));
   if (nt == 0 || ns == 0) return;
+  StageEvents E;
+  E.mark(0, st);
+  long launches0 = g_fmm_launches;
   auto t0 = Clock::now();
   std::vector<double> gap;
   build_trees(h, ns, src, q, nt, tgt, gap, st);
@@ -245,6 +263,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   for (int l = 0; l <= maxlev; ++l)
     for (int b = lvl[l]; b < lvl[l + 1]; ++b) has_level[bcomp[b]][l] = 1;
   h->stats.ms_tree = ms_since(t0);
+  E.mark(1, st);
   // ---- operators
   auto t1 = Clock::now();
   std::vector<CompGeom> cg(nc);
@@ -397,6 +416,14 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     FMM_CHECK(cudaStreamSynchronize(st));
   }
   h->stats.ms_operators = ms_since(t1);
+  h->stats.n_reac_classes = (long)rjobs.size();
+  h->stats.n_free_ops = (long)sep_m2l.size();
+  {
+    long tq = 0;
+    for (const ReacJob& j : rjobs) tq += j.Q;
+    h->stats.n_reac_T_nodes = tq;
+  }
+  E.mark(2, st);
   // ---- passes
   auto t2 = Clock::now();
   CompGeom* dcg = upload(ws.segl, cg, st);   // segl is free after the tree build
@@ -415,7 +442,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   cplx* M = need<cplx>(ws.M, (size_t)nb * P);
   cplx* L = need<cplx>(ws.L, (size_t)nb * P);
   // schedules
-  std::vector<int> p2m_leaves, l2p_leaves, near_leaves;
+  std::vector<int> p2m_leaves, l2p_leaves, near_free, near_reac;
   std::vector<std::vector<int>> m2m_lvl(23), m2l_lvl(23);
   for (int l = 0; l <= maxlev; ++l)
     for (int b = lvl[l]; b < lvl[l + 1]; ++b) {
@@ -427,13 +454,14 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
       }
       if (tgt_ && l >= 2) m2l_lvl[l].push_back(b);
       if (tgt_ && leaf) {
-        near_leaves.push_back(b);
+        (comps[bcomp[b]].kind == CK_FREE ? near_free : near_reac).push_back(b);
         if (l >= 2) l2p_leaves.push_back(b);
       }
     }
   std::vector<int> sched;
   auto push = [&](const std::vector<int>& v) { long o = sched.size(); sched.insert(sched.end(), v.begin(), v.end()); return o; };
-  long o_p2m = push(p2m_leaves), o_l2p = push(l2p_leaves), o_near = push(near_leaves);
+  long o_p2m = push(p2m_leaves), o_l2p = push(l2p_leaves), o_near_free = push(near_free),
+       o_near_reac = push(near_reac);
   std::vector<long> o_m2m(23), o_m2l(23);
   for (int l = 0; l <= maxlev; ++l) { o_m2m[l] = push(m2m_lvl[l]); o_m2l[l] = push(m2l_lvl[l]); }
   int* dsched = upload(ws.lvlcnt, sched, st);
@@ -444,6 +472,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   for (int l = maxlev; l >= 2; --l)
     launch_m2m(p, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, dm2m, shift_ops, M, st);
   FMM_CHECK(cudaGetLastError());
+  E.mark(3, st);
   // downward pass
   OpIndex OI;
   OI.m2l_base = dm2m + 2 * nc * 23;
@@ -454,12 +483,14 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     launch_m2l(p, dsched + o_m2l[l], (int)m2l_lvl[l].size(), l >= 3 ? 1 : 0, B, OI, loff, ws.vi.as<int>(),
                m2l_ops, shift_ops, M, L, err, st);
   FMM_CHECK(cudaGetLastError());
+  E.mark(4, st);
   cplx* phi = need<cplx>(ws.phi, std::max<long>(1, comps.empty() ? 1 : comps.back().to + comps.back().nt));
   long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;
   FMM_CHECK(cudaMemsetAsync(phi, 0, sizeof(cplx) * NT, st));
   launch_l2p(p, dsched + o_l2p, (int)l2p_leaves.size(), B, dcg, ws.tpos.as<double>(), L, phi, st);
   // near field
   cplx* coef = rule_coef(h, st);
+  E.mark(5, st);
   std::vector<NearComp> ncs(nc);
   for (int c = 0; c < nc; ++c) {
     const Comp& C_ = comps[c];
@@ -474,19 +505,41 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   NB.uo = loff + (nb + 1); NB.ui = ws.ui.as<int>();
   NB.wo = loff + 2 * (nb + 1); NB.wi = ws.wi.as<int>();
   NB.xo = loff + 3 * (nb + 1); NB.xi = ws.xi.as<int>();
-  launch_near(dsched + o_near, (int)near_leaves.size(), NB, dnc, make_rule_view(h->rule, coef),
-              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, st);
+  unsigned long long* counters = need<unsigned long long>(ws.iota, 4);
+  FMM_CHECK(cudaMemsetAsync(counters, 0, 32, st));
+  launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st);
+  E.mark(6, st);
+  launch_near(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, make_rule_view(h->rule, coef),
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 2, st);
   FMM_CHECK(cudaGetLastError());
+  E.mark(7, st);
   // sum of the components in their fixed order
   for (int c = 0; c < nc; ++c)
     launch_scatter_add(comps[c].nt, ws.tidx.as<int>() + comps[c].to, phi + comps[c].to, out, st);
   if (h->flags & FMM_NORM_PAPER) launch_norm_paper(nt, tgt, medium_of(h), out, st);
   FMM_CHECK(cudaGetLastError());
+  E.mark(8, st);
   int herr = 0;
+  unsigned long long hc[4];
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(hc, counters, 32, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
   if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair outside the interface band");
   h->stats.ms_eval = ms_since(t2);
+  h->stats.gpu_ms_tree = E.ms(0, 1);
+  h->stats.gpu_ms_operators = E.ms(1, 2);
+  h->stats.gpu_ms_upward = E.ms(2, 3);
+  h->stats.gpu_ms_m2l = E.ms(3, 4);
+  h->stats.gpu_ms_l2p = E.ms(4, 5);
+  h->stats.gpu_ms_near_free = E.ms(5, 6);
+  h->stats.gpu_ms_near_reac = E.ms(6, 7);
+  h->stats.gpu_ms_sum = E.ms(7, 8);
+  h->stats.gpu_ms_total = E.ms(0, 8);
+  h->stats.n_free_pairs = (long)hc[0];
+  h->stats.n_reac_pairs = (long)hc[2];
+  h->stats.n_reac_nodes = (long)hc[3];
+  h->stats.n_launches = g_fmm_launches - launches0;
 }
 
 extern "C" int fmm_layered_eval(fmm_layered_t* h, long ns, const double* src, const double* q, long nt,
@@ -536,6 +589,14 @@ extern "C" int fmm_layered_eval_host(fmm_layered_t* h, long ns, const double* sr
   }
   bs.release(); bq.release(); bt.release(); bo.release();
   return rc;
+}
+
+extern "C" int fmm_layered_measure_fp64_peak(double* gflops) {
+  if (!gflops) return FMM_ERR_ARG;
+  double v = measure_fp64_peak_impl();
+  if (!(v > 0)) return FMM_ERR_CUDA;
+  *gflops = v;
+  return FMM_OK;
 }
 
 // ---------------------------------------------------------------- export

@@ -132,6 +132,10 @@ struct fmm_layered {
   long nsrc_last = 0, ntgt_last = 0;
 };
 
+// Count of this library's kernel launches (CUB's internal launches excluded).
+extern long g_fmm_launches;
+#define LAUNCH(...) do { ++g_fmm_launches; __VA_ARGS__; } while (0)
+
 // ---- plain-data structures passed to kernels
 struct SepJob { double b[3]; double k; int kind; long out_off; };
 struct ReacJob {

@@ -178,13 +178,13 @@ static void upload_nodes(fmm_layered* h, const std::vector<cplx>& kr, const std:
   (void)q_from;
   if (h->L1 > 1) {
     dim3 grid((Q + 127) / 128, h->L1);
-    k_sigma<<<grid, 128, 0, st>>>(h->L1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(),
-                                  Q, 0, R.kr.as<cplx>(), R.kz.as<cplx>(), R.sigma.as<cplx>());
+    LAUNCH(k_sigma<<<grid, 128, 0, st>>>(h->L1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(),
+                                  Q, 0, R.kr.as<cplx>(), R.kz.as<cplx>(), R.sigma.as<cplx>()));
   } else {
     // single layer: only k_z is needed
     dim3 grid((Q + 127) / 128, 1);
-    k_sigma<<<grid, 128, 0, st>>>(1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(),
-                                  Q, 0, R.kr.as<cplx>(), R.kz.as<cplx>(), R.sigma.as<cplx>());
+    LAUNCH(k_sigma<<<grid, 128, 0, st>>>(1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(),
+                                  Q, 0, R.kr.as<cplx>(), R.kz.as<cplx>(), R.sigma.as<cplx>()));
   }
   FMM_CHECK(cudaGetLastError());
 }

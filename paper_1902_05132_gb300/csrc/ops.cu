@@ -441,11 +441,11 @@ void launch_gaunt(int p, const std::vector<double>& xg, const std::vector<double
   long total = (long)P * P * (2 * p + 1);
   cudaMemcpyAsync(dx, xg.data(), 8 * xg.size(), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dw, wg.data(), 8 * wg.size(), cudaMemcpyHostToDevice, st);
-  k_gaunt<<<(total + 127) / 128, 128, 0, st>>>(p, (int)xg.size(), dx, dw, G);
+  LAUNCH(k_gaunt<<<(total + 127) / 128, 128, 0, st>>>(p, (int)xg.size(), dx, dw, G));
 }
 
 void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st) {
-  if (njobs) k_sep_ops<<<njobs, 256, 0, st>>>(p, jobs, G, ops);
+  if (njobs) LAUNCH(k_sep_ops<<<njobs, 256, 0, st>>>(p, jobs, G, ops));
 }
 
 void launch_reac_T(int p, const ReacJob* jobs, int njobs, const Rule& R, cplx* ops, cudaStream_t st) {
@@ -456,8 +456,8 @@ void launch_reac_T(int p, const ReacJob* jobs, int njobs, const Rule& R, cplx* o
   int threads = 256;
   while ((p + 1) * P > 8 * threads && threads < 1024) threads *= 2;
   cudaFuncSetAttribute(k_reac_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_reac_T<<<grid, threads, smem, st>>>(p, jobs, R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(), R.Q(),
-                                        R.sigma.as<cplx>(), ops);
+  LAUNCH(k_reac_T<<<grid, threads, smem, st>>>(p, jobs, R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(), R.Q(),
+                                        R.sigma.as<cplx>(), ops));
 }
 
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
@@ -465,26 +465,26 @@ void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs,
   int P = (p + 1) * (p + 1);
   size_t smem = sizeof(cplx) * P2M_CHUNK * P;
   cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (n) k_p2m<<<n, 128, smem, st>>>(p, leaves, B, cgs, spos, sq, M);
+  if (n) LAUNCH(k_p2m<<<n, 128, smem, st>>>(p, leaves, B, cgs, spos, sq, M));
 }
 
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
                 const cplx* L, cplx* phi, cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  if (n) k_l2p<<<n, 128, sizeof(cplx) * P, st>>>(p, leaves, B, cgs, tpos, L, phi);
+  if (n) LAUNCH(k_l2p<<<n, 128, sizeof(cplx) * P, st>>>(p, leaves, B, cgs, tpos, L, phi));
 }
 
 void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, const cplx* ops, cplx* M,
                 cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  if (n) k_m2m<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, B, op_base, ops, M);
+  if (n) LAUNCH(k_m2m<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, B, op_base, ops, M));
 }
 
 void launch_m2l(int p, const int* boxes, int n, int with_l2l, BoxGeom B, OpIndex OI, const int* voff,
                 const int* vidx, const cplx* m2l_ops, const cplx* l2l_ops, const cplx* M, cplx* L, int* err,
                 cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  if (n) k_m2l<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, with_l2l, B, OI, voff, vidx, m2l_ops, l2l_ops, M, L, err);
+  if (n) LAUNCH(k_m2l<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, with_l2l, B, OI, voff, vidx, m2l_ops, l2l_ops, M, L, err));
 }
 
 void launch_phase_expand(int p, const ExpandJob* jobs, int njobs, const cplx* src, cplx* dst, cudaStream_t st) {
@@ -492,6 +492,6 @@ void launch_phase_expand(int p, const ExpandJob* jobs, int njobs, const cplx* sr
   for (int j0 = 0; j0 < njobs; j0 += 60000) {
     int nj = njobs - j0 < 60000 ? njobs - j0 : 60000;
     dim3 grid((unsigned)((PP + 255) / 256), nj);
-    k_phase_expand<<<grid, 256, 0, st>>>(p, jobs + j0, src, dst);
+    LAUNCH(k_phase_expand<<<grid, 256, 0, st>>>(p, jobs + j0, src, dst));
   }
 }

@@ -34,8 +34,9 @@ __device__ inline cplx j0c(cplx z) {
 
 // One reaction pair on the rule (coef already holds sigma for the component).
 __device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coef, const cplx* __restrict__ kzl,
-                                 const cplx* __restrict__ kzp, double rho, double zt, double zs) {
+                                 const cplx* __restrict__ kzp, double rho, double zt, double zs, int* nq_out = nullptr) {
   int nq = rule_nodes(R, R.ta + TAIL_DECAY / (zt + zs));
+  if (nq_out) *nq_out = nq;
   cplx acc = C(0, 0);
   for (int q = 0; q < R.n_near; ++q) {
     cplx e = cexp_(cadd(cmul(C(0, zt), kzl[q]), cmul(C(0, zs), kzp[q])));
@@ -59,7 +60,9 @@ __device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coe
 #define NEAR_CHUNK 128
 __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearComp* __restrict__ ncs,
                        RuleView R, const double* __restrict__ spos, const cplx* __restrict__ sq,
-                       const double* __restrict__ tpos, cplx* __restrict__ phi) {
+                       const double* __restrict__ tpos, cplx* __restrict__ phi,
+                       unsigned long long* __restrict__ counters) {
+  unsigned long long my_pairs = 0, my_nodes = 0;
   int T = leaves[blockIdx.x];
   const NearComp nc = ncs[B.comp[T]];
   __shared__ double sx[NEAR_CHUNK], sy[NEAR_CHUNK], sz[NEAR_CHUNK];
@@ -108,6 +111,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
               sincos(nc.k * r, &s, &c);
               double f = 1.0 / (4.0 * FMM_PI * r);
               cfma(acc, C(c * f, s * f), sqs[k]);
+              ++my_pairs;
             }
           } else {
             double zt = fabs(z - nc.dref);
@@ -115,13 +119,20 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
               double dx = x - sx[k], dy = y - sy[k];
               double rho = sqrt(dx * dx + dy * dy);
               double zs = fabs(sz[k] - nc.dref);
-              cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs), sqs[k]);
+              int nq;
+              cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs, &nq), sqs[k]);
+              ++my_pairs;
+              my_nodes += nq;
             }
           }
         }
       }
     }
     if (act) phi[t] = cadd(phi[t], acc);
+  }
+  if (counters && my_pairs) {
+    atomicAdd(&counters[0], my_pairs);
+    atomicAdd(&counters[1], my_nodes);
   }
 }
 
@@ -228,8 +239,8 @@ __global__ void k_norm_paper(long n, const double* __restrict__ tgt, DirectMediu
 // ---------------------------------------------------------------- launchers
 void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st) {
   long total = (long)L1 * L1 * 4 * R.Q();
-  k_coef<<<(total + 255) / 256, 256, 0, st>>>(L1, R.Q(), R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(),
-                                              R.sigma.as<cplx>(), coef);
+  LAUNCH(k_coef<<<(total + 255) / 256, 256, 0, st>>>(L1, R.Q(), R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(),
+                                              R.sigma.as<cplx>(), coef));
 }
 
 RuleView make_rule_view(const Rule& R, const cplx* coef) {
@@ -247,19 +258,56 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
-                 const cplx* sq, const double* tpos, cplx* phi, cudaStream_t st) {
-  if (n) k_near<<<n, 64, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi);
+                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st) {
+  if (n) LAUNCH(k_near<<<n, 64, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
+}
+
+// Dependent FP64 FMA chains (8 independent chains per thread).
+__global__ void k_fp64_peak(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+double measure_fp64_peak_impl() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int blocks = nsm * 8, threads = 256, iters = 20000;
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * blocks * threads) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    LAUNCH(k_fp64_peak<<<blocks, threads>>>(d, iters, 0.999999, 1e-7));
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  return 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e6);
 }
 
 void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
                    RuleView R, const cplx* coef_all, double* out, cudaStream_t st) {
-  if (nt) k_direct<<<(nt + 63) / 64, 64, 0, st>>>(nt, tgt, ns, src, q, md, R, coef_all, out);
+  if (nt) LAUNCH(k_direct<<<(nt + 63) / 64, 64, 0, st>>>(nt, tgt, ns, src, q, md, R, coef_all, out));
 }
 
 void launch_scatter_add(long n, const int* tidx, const cplx* phi, double* out, cudaStream_t st) {
-  if (n) k_scatter_add<<<(n + 255) / 256, 256, 0, st>>>(n, tidx, phi, out);
+  if (n) LAUNCH(k_scatter_add<<<(n + 255) / 256, 256, 0, st>>>(n, tidx, phi, out));
 }
 
 void launch_norm_paper(long n, const double* tgt, DirectMedium md, double* out, cudaStream_t st) {
-  if (n) k_norm_paper<<<(n + 255) / 256, 256, 0, st>>>(n, tgt, md, out);
+  if (n) LAUNCH(k_norm_paper<<<(n + 255) / 256, 256, 0, st>>>(n, tgt, md, out));
 }

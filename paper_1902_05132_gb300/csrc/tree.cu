@@ -472,8 +472,8 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     FMM_CHECK(cudaMemsetAsync(counts, 0, 4 * 2 * L1, st));
     FMM_CHECK(cudaMemsetAsync(flags, 0, 4, st));
   }
-  if (ns) k_classify<<<(ns + 255) / 256, 256, 0, st>>>(ns, src, q, 0, L1, h->d_d.as<double>(), sl, counts, bbox, gap, flags);
-  if (nt) k_classify<<<(nt + 255) / 256, 256, 0, st>>>(nt, tgt, nullptr, 1, L1, h->d_d.as<double>(), tl, counts, bbox, gap, flags);
+  if (ns) LAUNCH(k_classify<<<(ns + 255) / 256, 256, 0, st>>>(ns, src, q, 0, L1, h->d_d.as<double>(), sl, counts, bbox, gap, flags));
+  if (nt) LAUNCH(k_classify<<<(nt + 255) / 256, 256, 0, st>>>(nt, tgt, nullptr, 1, L1, h->d_d.as<double>(), tl, counts, bbox, gap, flags));
   FMM_CHECK(cudaGetLastError());
   // stable partition of points by layer
   int* sorder = need<int>(ws.sorder, ns);
@@ -612,10 +612,10 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     CompDev cs = cdev[ci];
     int sl_ = (c.kind == CK_FREE) ? c.l : c.lp;
     cs.zlo = c.zs_lo; cs.zhi = c.zs_hi;
-    if (c.ns) k_gather_src<<<(c.ns + 255) / 256, 256, 0, st>>>(c.ns, sorder + soff[sl_], src, q, cs, c.so, spos_u, sq_u, skey_u, sval_u, sidx_u);
+    if (c.ns) LAUNCH(k_gather_src<<<(c.ns + 255) / 256, 256, 0, st>>>(c.ns, sorder + soff[sl_], src, q, cs, c.so, spos_u, sq_u, skey_u, sval_u, sidx_u));
     CompDev ct = cdev[ci];
     ct.zlo = c.zt_lo; ct.zhi = c.zt_hi;
-    if (c.nt) k_gather_tgt<<<(c.nt + 255) / 256, 256, 0, st>>>(c.nt, torder + toff[c.l], tgt, ct, c.to, tpos_u, tkey_u, tval_u, tidx_u);
+    if (c.nt) LAUNCH(k_gather_tgt<<<(c.nt + 255) / 256, 256, 0, st>>>(c.nt, torder + toff[c.l], tgt, ct, c.to, tpos_u, tkey_u, tval_u, tidx_u));
   }
   FMM_CHECK(cudaGetLastError());
   // ---- segmented stable sort by key (radix sort is stable; values are the
@@ -655,8 +655,8 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
   double* tpos = need<double>(ws.tpos, 3 * NT);
   int* tidx = need<int>(ws.tidx, NT);
   int* tlocal = need<int>(ws.tlocal, NT);
-  if (NS) k_permute<<<(NS + 255) / 256, 256, 0, st>>>(NS, sperm, spos_u, sq_u, sidx_u, spos, sqs, sidx, slocal, dsegl, nc);
-  if (NT) k_permute<<<(NT + 255) / 256, 256, 0, st>>>(NT, tperm, tpos_u, nullptr, tidx_u, tpos, nullptr, tidx, tlocal, dsegl + nc + 1, nc);
+  if (NS) LAUNCH(k_permute<<<(NS + 255) / 256, 256, 0, st>>>(NS, sperm, spos_u, sq_u, sidx_u, spos, sqs, sidx, slocal, dsegl, nc));
+  if (NT) LAUNCH(k_permute<<<(NT + 255) / 256, 256, 0, st>>>(NT, tperm, tpos_u, nullptr, tidx_u, tpos, nullptr, tidx, tlocal, dsegl + nc + 1, nc));
   FMM_CHECK(cudaGetLastError());
 
   // ---- tree levels
@@ -706,9 +706,9 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     if (n == 0) break;
     int* cntl = need<int>(ws.lvlcnt, n + 1);
     int* scn = need<int>(ws.lvlscan, n + 1);
-    k_count_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, h->leaf, ws.bsb.as<int>(), ws.bse.as<int>(),
+    LAUNCH(k_count_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, h->leaf, ws.bsb.as<int>(), ws.bse.as<int>(),
                                                       ws.btb.as<int>(), ws.bte.as<int>(), ws.bprefix.as<unsigned long long>(),
-                                                      skey, tkey, cntl);
+                                                      skey, tkey, cntl));
     exclusive_scan(ws, cntl, scn, n, st);
     int last_cnt = 0, last_scan = 0;
     FMM_CHECK(cudaMemcpyAsync(&last_cnt, cntl + n - 1, 4, cudaMemcpyDeviceToHost, st));
@@ -716,10 +716,10 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     FMM_CHECK(cudaStreamSynchronize(st));
     int total = last_cnt + last_scan;
     grow_boxes((size_t)le + total, (size_t)le);
-    k_write_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, le, scn, cntl, ws.bcomp.as<int>(), ws.blevel.as<int>(),
+    LAUNCH(k_write_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, le, scn, cntl, ws.bcomp.as<int>(), ws.blevel.as<int>(),
                                                       ws.bprefix.as<unsigned long long>(), ws.bsb.as<int>(), ws.bse.as<int>(),
                                                       ws.btb.as<int>(), ws.bte.as<int>(), ws.bparent.as<int>(),
-                                                      ws.bchild0.as<int>(), ws.bnchild.as<int>(), ws.bcoord.as<int>(), skey, tkey);
+                                                      ws.bchild0.as<int>(), ws.bnchild.as<int>(), ws.bcoord.as<int>(), skey, tkey));
     FMM_CHECK(cudaGetLastError());
     if (total == 0) break;
     lvl.push_back(le + total);
@@ -739,8 +739,8 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
   int* cnt = need<int>(ws.lcnt, 4 * (size_t)nb + 4);
   int* off = need<int>(ws.loff, 4 * ((size_t)nb + 1));
   FMM_CHECK(cudaMemsetAsync(flags, 0, 4, st));
-  k_lists<false><<<(nb + 127) / 128, 128, 0, st>>>(nb, T, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                   nullptr, nullptr, flags);
+  LAUNCH(k_lists<false><<<(nb + 127) / 128, 128, 0, st>>>(nb, T, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr, nullptr, flags));
   FMM_CHECK(cudaGetLastError());
   std::vector<int> tot(4);
   for (int k = 0; k < 4; ++k) {
@@ -762,8 +762,8 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
   int* ui = need<int>(ws.ui, tot[1]);
   int* wi = need<int>(ws.wi, tot[2]);
   int* xi = need<int>(ws.xi, tot[3]);
-  k_lists<true><<<(nb + 127) / 128, 128, 0, st>>>(nb, T, nullptr, off, off + (nb + 1), off + 2 * (size_t)(nb + 1),
-                                                  off + 3 * (size_t)(nb + 1), vi, ui, wi, xi, flags);
+  LAUNCH(k_lists<true><<<(nb + 127) / 128, 128, 0, st>>>(nb, T, nullptr, off, off + (nb + 1), off + 2 * (size_t)(nb + 1),
+                                                  off + 3 * (size_t)(nb + 1), vi, ui, wi, xi, flags));
   FMM_CHECK(cudaGetLastError());
   FMM_CHECK(cudaMemcpyAsync(&hflags, flags, 4, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
