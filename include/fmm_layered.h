@@ -139,6 +139,34 @@ int fmm_layered_direct(fmm_layered_t* h, long n_src, const double* src_xyz,
                        double* out, void* stream);
 
 /*
+ * Allocation-free direct sum.  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory when they need the potentials,
+ * for example code running inside another framework's memory manager (whose
+ * caching allocator holds the free device memory) or an inner solver loop
+ * that must not call cudaMalloc/cudaFree (they synchronize the device).
+ * Computes exactly what fmm_layered_direct computes (same arguments, device
+ * buffers, result on `stream`) but keeps its scratch -- the per-node reaction
+ * coefficients, interface-distance reductions and error flags -- in one
+ * file-scope device array of FMM_NOALLOC_SCRATCH_BYTES, held by every GPU
+ * that loads the library until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and the array keeps the last call's
+ *     contents (the call clears what must start at zero): calls that overlap
+ *     on the GPU (several streams or threads at once) race; serialize them.
+ *   - Limit: the coefficient table needs 64 * n_layers^2 * Q bytes (Q = nodes
+ *     of the handle's quadrature rule); larger tables are rejected with
+ *     FMM_ERR_UNSUPPORTED and a message, as is a geometry whose points lie so
+ *     close to an interface that the rule would have to grow (run
+ *     fmm_layered_direct or fmm_layered_eval once on that geometry first).
+ */
+#define FMM_NOALLOC_SCRATCH_BYTES (4 * 1024 * 1024)
+int fmm_layered_direct_noalloc(fmm_layered_t* h, long n_src, const double* src_xyz,
+                               const double* charges, long n_tgt, const double* tgt_xyz,
+                               double* out, void* stream);
+
+/*
  * Throughput of dependent FP64 fused multiply-adds on the current device
  * (GFLOP/s, 2 flops per FMA), measured by a short kernel; the denominator of
  * the FP64 roofline.  Returns FMM_OK and writes *gflops.

@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
             "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
             "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
-            "fmm_layered_measure_fp64_peak"]
+            "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc"]
 
 _lib = None
 
@@ -68,7 +68,8 @@ def lib():
     L.fmm_layered_destroy.restype = None
     L.fmm_layered_last_error.argtypes = [v]
     L.fmm_layered_last_error.restype = ctypes.c_char_p
-    for name in ("fmm_layered_eval", "fmm_layered_eval_host", "fmm_layered_direct"):
+    for name in ("fmm_layered_eval", "fmm_layered_eval_host", "fmm_layered_direct",
+                 "fmm_layered_direct_noalloc"):
         f = getattr(L, name)
         f.argtypes = [v, l, d, d, l, d, d, v]
         f.restype = i
@@ -154,6 +155,12 @@ class LayeredFMM:
     def direct(self, src, q, tgt, out=None, stream=None):
         """All-pairs direct sum on the GPU (device tensors)."""
         return self._call_dev(lib().fmm_layered_direct, src, q, tgt, out, stream)
+
+    def direct_noalloc(self, src, q, tgt, out=None, stream=None):
+        """Direct sum that allocates no device memory (fixed library scratch;
+        see fmm_layered_direct_noalloc).  Pass ``out`` to avoid the one torch
+        allocation this wrapper would otherwise make for the result."""
+        return self._call_dev(lib().fmm_layered_direct_noalloc, src, q, tgt, out, stream)
 
     def eval_host(self, src, q, tgt, stream=None):
         """FMM with host (numpy) buffers: copies in, evaluates, copies back."""
