@@ -19,9 +19,14 @@ Tree (reading c8 of the ambiguities; the paper leaves it to DASHMM):
   interleaved x lowest; in reaction trees targets are clamped to the target
   half (i_z >= 2^20 when targets lie above the interface) and images to the
   other half.  Stable sort by (key, original index), sources and targets
-  separately.  A box at level l is refined iff it holds more than ``leaf``
-  sources or more than ``leaf`` targets and l < 21; empty children are
-  dropped.  Boxes are numbered by (level, key prefix).
+  separately.  A box at level l < 21 is refined iff it holds more than ``leaf``
+  sources or more than ``leaf`` targets, or -- in a reaction tree -- it touches
+  the interface (its closed z-extent contains the root's mid-plane) and holds
+  any point; empty children are dropped.  The second rule separates every
+  target leaf from every image leaf by at least one box, so the reaction
+  components need no near-field evaluation as long as no point lies within
+  2^-21 of the root width of the interface (design reading; the paper leaves
+  the refinement to DASHMM).  Boxes are numbered by (level, key prefix).
 Lists (Cheng-Greengard-Rokhlin style, source boxes with >= 1 source, target
   boxes with >= 1 target; closed boxes touching = adjacent):
   V(T): children of the parent's colleagues not adjacent to T (M2L);
@@ -116,10 +121,11 @@ def point_keys(pos, c, h, zclamp=None):
 class Tree:
     """Adaptive octree over one component's sources and targets."""
 
-    def __init__(self, src, tgt, leaf, c, h, zclamp_src=None, zclamp_tgt=None):
+    def __init__(self, src, tgt, leaf, c, h, zclamp_src=None, zclamp_tgt=None, split_interface=False):
         self.c = np.asarray(c, float)
         self.h = float(h)
         self.leaf = int(leaf)
+        self.split_interface = bool(split_interface)
         ks = point_keys(src, self.c, self.h, zclamp_src) if len(src) else np.zeros(0, np.uint64)
         kt = point_keys(tgt, self.c, self.h, zclamp_tgt) if len(tgt) else np.zeros(0, np.uint64)
         # stable sort by (key, original index)
@@ -144,7 +150,12 @@ class Tree:
                 pre.append(p)
                 s0.append(a0); s1.append(a1); t0.append(b0); t1.append(b1); par.append(pa)
                 me = base + j
-                if ((a1 - a0) > self.leaf or (b1 - b0) > self.leaf) and level < MAXLEV:
+                touches = False
+                if self.split_interface and (a1 - a0) + (b1 - b0) > 0:
+                    iz = demorton(p, level)[2]
+                    half = 1 << (level - 1) if level >= 1 else 0
+                    touches = level == 0 or iz == half - 1 or iz == half
+                if ((a1 - a0) > self.leaf or (b1 - b0) > self.leaf or touches) and level < MAXLEV:
                     sp_ = self._prefix(self.skeys[a0:a1], level + 1)
                     tp_ = self._prefix(self.tkeys[b0:b1], level + 1)
                     for o in range(8):
@@ -496,7 +507,7 @@ def component_tree(medium, comp, src, tgt, leaf):
         zt, zs = (half, 2 ** NBITS - 1), (0, half - 1)
     else:
         zt, zs = (0, half - 1), (half, 2 ** NBITS - 1)
-    return Tree(src, tgt, leaf, c, h, zclamp_src=zs, zclamp_tgt=zt)
+    return Tree(src, tgt, leaf, c, h, zclamp_src=zs, zclamp_tgt=zt, split_interface=True)
 
 
 # ============================================================== evaluation

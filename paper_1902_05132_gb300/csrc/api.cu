@@ -12,15 +12,17 @@
 void launch_gaunt(int p, const std::vector<double>& xg, const std::vector<double>& wg, double* G, double* dx,
                   double* dw, cudaStream_t st);
 void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st);
-void launch_reac_T(int p, const ReacJob* jobs, int njobs, const Rule& R, cplx* ops, cudaStream_t st);
+void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const double* d_rho, const long* d_out_off,
+                       cplx* ops, DevBuf& scratch, cudaStream_t st);
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
                 const cplx* sq, cplx* M, cudaStream_t st);
 void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, const cplx* ops, cplx* M,
                 cudaStream_t st);
 void launch_m2l(int p, const int* boxes, int n, int with_l2l, BoxGeom B, OpIndex OI, const int* voff,
-                const int* vidx, const cplx* m2l_ops, const cplx* l2l_ops, const cplx* M, cplx* L, int* err,
-                cudaStream_t st);
-void launch_phase_expand(int p, const ExpandJob* jobs, int njobs, const cplx* src, cplx* dst, cudaStream_t st);
+                const int* vidx, const cplx* free_ops, const cplx* l2l_ops, const cplx* reac_ops, const cplx* M,
+                cplx* L, int* err, cudaStream_t st);
+void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
+                      int* err, cudaStream_t st);
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
                 const cplx* L, cplx* phi, cudaStream_t st);
 void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st);
@@ -143,6 +145,9 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
                    &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
                    &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.cub_tmp};
   for (DevBuf* b : wsb) b->release();
+  h->cache.free_buf.release();
+  h->cache.shift_buf.release();
+  h->cache.rad_buf.release();
   delete h;
 }
 
@@ -208,15 +213,8 @@ extern "C" int fmm_layered_direct(fmm_layered_t* h, long ns, const double* src, 
 }
 
 // ---------------------------------------------------------------- eval
-static const int RHO2[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
-static int rho2_index(int r2) {
-  for (int i = 0; i < 10; ++i) if (RHO2[i] == r2) return i;
-  return -1;
-}
-
 struct StageEvents {
   cudaEvent_t ev[10];
-  int n = 0;
   StageEvents() { for (auto& e : ev) cudaEventCreate(&e); }
   ~StageEvents() { for (auto& e : ev) cudaEventDestroy(e); }
   void mark(int i, cudaStream_t st) { cudaEventRecord(ev[i], st); }
@@ -227,9 +225,26 @@ struct StageEvents {
   }
 };
 
+static const int RHO2[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+
+static uint64_t dbits(double x) {
+  uint64_t u;
+  memcpy(&u, &x, 8);
+  return u;
+}
+
+// Append n operators of P^2 elements to a cache buffer (device contents kept).
+static long cache_alloc(DevBuf& buf, long& used, long n_elems, cudaStream_t st) {
+  long off = used;
+  buf.grow_keep(sizeof(cplx) * (size_t)(used + n_elems), sizeof(cplx) * (size_t)used, st);
+  used += n_elems;
+  return off;
+}
+
 static void eval_impl(fmm_layered* h, long ns, const double* src, const double* q, long nt, const double* tgt,
                       double* out, cudaStream_t st) {
   Workspace& ws = h->ws;
+  OpCache& oc = h->cache;
   const int p = h->p, P = (p + 1) * (p + 1);
   const long PP = (long)P * P;
   FMM_CHECK(cudaMemsetAsync(out, 0, sizeof(double) * 2 * nt, st));
@@ -246,26 +261,6 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   const std::vector<int>& lvl = h->lvl_begin;
   int maxlev = 0;
   while (maxlev + 1 < 22 && lvl[maxlev + 2] > lvl[maxlev + 1]) ++maxlev;
-  // host copies needed for scheduling
-  std::vector<int> bcomp(nb), bnchild(nb), bsb(nb), bse(nb), btb(nb), bte(nb);
-  FMM_CHECK(cudaMemcpyAsync(bcomp.data(), ws.bcomp.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(bnchild.data(), ws.bnchild.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(bsb.data(), ws.bsb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(bse.data(), ws.bse.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(btb.data(), ws.btb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(bte.data(), ws.bte.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
-  std::vector<int> uo(nb + 1);
-  FMM_CHECK(cudaMemcpyAsync(uo.data(), ws.loff.as<int>() + (nb + 1), 4 * (nb + 1), cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaStreamSynchronize(st));
-  h->stats.n_u_pairs = uo[nb];
-  // per component: levels present
-  std::vector<std::vector<char>> has_level(nc, std::vector<char>(23, 0));
-  for (int l = 0; l <= maxlev; ++l)
-    for (int b = lvl[l]; b < lvl[l + 1]; ++b) has_level[bcomp[b]][l] = 1;
-  h->stats.ms_tree = ms_since(t0);
-  E.mark(1, st);
-  // ---- operators
-  auto t1 = Clock::now();
   std::vector<CompGeom> cg(nc);
   int nfree = 0, nreac = 0;
   for (int c = 0; c < nc; ++c) {
@@ -280,168 +275,229 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     cg[c].free_idx = (C_.kind == CK_FREE) ? nfree++ : -1;
     cg[c].reac_idx = (C_.kind == CK_REAC) ? nreac++ : -1;
   }
-  std::vector<long> m2m_base(nc * 23, -1), l2l_base(nc * 23, -1), m2l_base(nc * 23, -1);
-  std::vector<SepJob> sep;
-  long off_shift = 0, off_m2l = 0;
-  std::vector<SepJob> sep_m2l;
-  for (int c = 0; c < nc; ++c) {
-    for (int l = 3; l <= maxlev; ++l) {
-      if (!has_level[c][l]) continue;
-      double w = cg[c].h2 / (double)(1 << l);
-      // M2M: child at level l into parent at level l-1 (source k); L2L (target k)
-      m2m_base[c * 23 + l] = off_shift;
-      for (int o = 0; o < 8; ++o) {
-        SepJob j{};
-        for (int a = 0; a < 3; ++a) j.b[a] = (((o >> a) & 1) ? 0.5 : -0.5) * w;
-        j.k = cg[c].ks;
-        j.kind = 1;
-        j.out_off = off_shift + (long)o * PP;
-        sep.push_back(j);
-      }
-      off_shift += 8 * PP;
-      l2l_base[c * 23 + l] = off_shift;
-      for (int o = 0; o < 8; ++o) {
-        SepJob j{};
-        for (int a = 0; a < 3; ++a) j.b[a] = (((o >> a) & 1) ? 0.5 : -0.5) * w;
-        j.k = cg[c].kt;
-        j.kind = 2;
-        j.out_off = off_shift + (long)o * PP;
-        sep.push_back(j);
-      }
-      off_shift += 8 * PP;
+  CompGeom* dcg = upload(ws.segl, cg, st);   // segl is free after the tree build
+  BoxGeom B;
+  B.comp = ws.bcomp.as<int>(); B.lev = ws.blevel.as<int>(); B.sb = ws.bsb.as<int>(); B.se = ws.bse.as<int>();
+  B.tb = ws.btb.as<int>(); B.te = ws.bte.as<int>(); B.parent = ws.bparent.as<int>();
+  B.child0 = ws.bchild0.as<int>(); B.nchild = ws.bnchild.as<int>(); B.coord = ws.bcoord.as<int>();
+  const int* loff = ws.loff.as<int>();
+  // reaction M2L classes used by the V lists
+  unsigned char* dused = need<unsigned char>(ws.lvlcnt, (size_t)nc * 23 * 40);
+  int* err = need<int>(ws.flags, 1);
+  FMM_CHECK(cudaMemsetAsync(dused, 0, (size_t)nc * 23 * 40, st));
+  FMM_CHECK(cudaMemsetAsync(err, 0, 4, st));
+  launch_mark_reac(nb, B, dcg, loff, ws.vi.as<int>(), dused, err, st);
+  FMM_CHECK(cudaGetLastError());
+  // host copies needed for scheduling
+  std::vector<int> bcomp(nb), bnchild(nb), bsb(nb), bse(nb), btb(nb), bte(nb);
+  std::vector<unsigned char> used((size_t)nc * 23 * 40);
+  FMM_CHECK(cudaMemcpyAsync(bcomp.data(), ws.bcomp.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bnchild.data(), ws.bnchild.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bsb.data(), ws.bsb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bse.data(), ws.bse.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(btb.data(), ws.btb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bte.data(), ws.bte.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(used.data(), dused, used.size(), cudaMemcpyDeviceToHost, st));
+  std::vector<int> lo_all(4 * (size_t)(nb + 1));
+  FMM_CHECK(cudaMemcpyAsync(lo_all.data(), ws.loff.ptr, 4 * lo_all.size(), cudaMemcpyDeviceToHost, st));
+  int herr0 = 0;
+  FMM_CHECK(cudaMemcpyAsync(&herr0, err, 4, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaStreamSynchronize(st));
+  if (herr0) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair outside the interface band");
+  const int* uo = lo_all.data() + (nb + 1);
+  h->stats.n_u_pairs = uo[nb];
+  // does any reaction component need near-field (direct) interactions?
+  bool reac_near = false;
+  for (int b = 0; b < nb && !reac_near; ++b) {
+    if (comps[bcomp[b]].kind != CK_REAC) continue;
+    for (int k = 1; k < 4; ++k) {
+      const int* o = lo_all.data() + (size_t)k * (nb + 1);
+      if (o[b + 1] > o[b]) { reac_near = true; break; }
     }
   }
-  // free-space M2L operators: 343 slots per (component, level >= 2)
-  std::vector<ReacJob> rjobs;
-  std::vector<ExpandJob> expand;
-  long off_radial = 0;
-  double wmin_reac = INFINITY;
+  std::vector<std::vector<char>> has_level(nc, std::vector<char>(23, 0));
+  for (int l = 0; l <= maxlev; ++l)
+    for (int b = lvl[l]; b < lvl[l + 1]; ++b) has_level[bcomp[b]][l] = 1;
+  h->stats.ms_tree = ms_since(t0);
+  E.mark(1, st);
+  // ---- operators (cached across evaluations)
+  auto t1 = Clock::now();
+  {
+    size_t bytes = sizeof(cplx) * (size_t)(oc.free_used + oc.shift_used + oc.rad_used);
+    if (bytes > (size_t)8 << 30) oc.clear();        // keep the cache bounded
+  }
+  std::vector<long> m2m_base(nc * 23, -1), l2l_base(nc * 23, -1), m2l_base(nc * 23, -1);
+  std::vector<long> reac_off((size_t)nc * 23 * 40, -1);
+  std::vector<SepJob> sep_shift, sep_free;
   for (int c = 0; c < nc; ++c) {
     for (int l = 2; l <= maxlev; ++l) {
       if (!has_level[c][l]) continue;
       double w = cg[c].h2 / (double)(1 << l);
-      if (comps[c].kind == CK_FREE) {
-        m2l_base[c * 23 + l] = off_m2l;
-        for (int dz = -3; dz <= 3; ++dz)
-          for (int dy = -3; dy <= 3; ++dy)
-            for (int dx = -3; dx <= 3; ++dx) {
-              int slot = ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
-              if (std::max(abs(dx), std::max(abs(dy), abs(dz))) < 2) continue;
+      if (l >= 3) {
+        for (int kind = 1; kind <= 2; ++kind) {
+          double k = (kind == 1) ? cg[c].ks : cg[c].kt;
+          auto key = std::make_tuple(dbits(k), dbits(w), kind);
+          auto it = oc.shift.find(key);
+          long off;
+          if (it == oc.shift.end()) {
+            off = cache_alloc(oc.shift_buf, oc.shift_used, 8 * PP, st);
+            oc.shift[key] = off;
+            for (int o = 0; o < 8; ++o) {
               SepJob j{};
-              j.b[0] = dx * w; j.b[1] = dy * w; j.b[2] = dz * w;
-              j.k = cg[c].kt;
-              j.kind = 0;
-              j.out_off = off_m2l + slot * PP;
-              sep_m2l.push_back(j);
+              for (int a = 0; a < 3; ++a) j.b[a] = (((o >> a) & 1) ? 0.5 : -0.5) * w;
+              j.k = k;
+              j.kind = kind;
+              j.out_off = off + (long)o * PP;
+              sep_shift.push_back(j);
             }
-        off_m2l += 343 * PP;
-      } else {
-        wmin_reac = std::min(wmin_reac, w);
-        m2l_base[c * 23 + l] = off_m2l;
-        const Comp& C_ = comps[c];
-        long sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b);   // * Q later
-        for (int jt = 0; jt < 2; ++jt)
-          for (int js = 0; js < 2; ++js) {
-            long radial_of[10];
-            for (int r = 0; r < 10; ++r) radial_of[r] = -1;
-            for (int r = 0; r < 10; ++r) {
-              if (jt == 0 && js == 0 && RHO2[r] < 4) continue;
-              ReacJob j{};
-              j.l = C_.l; j.lp = C_.lp; j.a = C_.a; j.b = C_.b;
-              j.kl = h->k[C_.l]; j.klp = h->k[C_.lp];
-              j.zt = (jt + 0.5) * w;
-              j.zs = (js + 0.5) * w;
-              j.rho = sqrt((double)RHO2[r]) * w;
-              j.phi = 0.0;
-              j.out_off = off_radial;
-              j.sig_off = sig_off;        // completed below
-              j.Q = 0;                    // completed below
-              radial_of[r] = off_radial;
-              off_radial += PP;
-              rjobs.push_back(j);
-            }
+          } else {
+            off = it->second;
+          }
+          (kind == 1 ? m2m_base : l2l_base)[c * 23 + l] = off;
+        }
+      }
+      if (comps[c].kind == CK_FREE) {
+        auto key = std::make_pair(dbits(cg[c].kt), dbits(w));
+        auto it = oc.free_m2l.find(key);
+        long off;
+        if (it == oc.free_m2l.end()) {
+          off = cache_alloc(oc.free_buf, oc.free_used, 343 * PP, st);
+          oc.free_m2l[key] = off;
+          for (int dz = -3; dz <= 3; ++dz)
             for (int dy = -3; dy <= 3; ++dy)
               for (int dx = -3; dx <= 3; ++dx) {
-                int r = rho2_index(dx * dx + dy * dy);
-                if (r < 0 || radial_of[r] < 0) continue;
-                int slot = ((jt * 2 + js) * 7 + (dy + 3)) * 7 + (dx + 3);
-                expand.push_back({radial_of[r], off_m2l + slot * PP, atan2((double)dy, (double)dx)});
+                if (std::max(abs(dx), std::max(abs(dy), abs(dz))) < 2) continue;
+                SepJob j{};
+                j.b[0] = dx * w; j.b[1] = dy * w; j.b[2] = dz * w;
+                j.k = cg[c].kt;
+                j.kind = 0;
+                j.out_off = off + (((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3)) * PP;
+                sep_free.push_back(j);
               }
-          }
-        off_m2l += 196 * PP;
+        } else {
+          off = it->second;
+        }
+        m2l_base[c * 23 + l] = off;
       }
     }
   }
-  // make the rule long enough for the reaction operators and near field
+  // reaction radial operators: only classes present, computed once per geometry
+  struct Pending { int c, l, jt, js; std::vector<int> rs; std::vector<long> offs; };
+  std::vector<Pending> pend;
   double tmax = h->rule.ta;
-  if (std::isfinite(wmin_reac)) tmax = std::max(tmax, h->rule.ta + (30.0 + 7.0 * p) / wmin_reac);
+  for (int c = 0; c < nc; ++c) {
+    if (comps[c].kind != CK_REAC) continue;
+    for (int l = 2; l <= maxlev; ++l) {
+      double w = cg[c].h2 / (double)(1 << l);
+      for (int g = 0; g < 4; ++g) {
+        Pending pd{c, l, g / 2, g % 2, {}, {}};
+        for (int r = 0; r < 10; ++r) {
+          if (!used[((size_t)c * 23 + l) * 40 + g * 10 + r]) continue;
+          const Comp& C_ = comps[c];
+          auto key = std::make_tuple(C_.l, C_.lp, C_.a, C_.b, dbits(w), pd.jt, pd.js, r);
+          auto it = oc.rad.find(key);
+          if (it != oc.rad.end()) {
+            reac_off[((size_t)c * 23 + l) * 40 + g * 10 + r] = it->second;
+          } else {
+            pd.rs.push_back(r);
+          }
+        }
+        if (!pd.rs.empty()) {
+          pend.push_back(pd);
+          double H = (pd.jt + pd.js + 1) * w;
+          tmax = std::max(tmax, h->rule.ta + (30.0 + 7.0 * p) / H);
+        }
+      }
+    }
+  }
+  // the near field needs the rule up to ta + 30 / (smallest vertical gap)
   double gmin = INFINITY, smin = INFINITY;
   for (int l = 0; l < h->L1; ++l)
     for (int sd = 0; sd < 2; ++sd) {
       smin = fmin(smin, gap[(0 * h->L1 + l) * 2 + sd]);
       gmin = fmin(gmin, gap[(1 * h->L1 + l) * 2 + sd]);
     }
-  if (h->L1 > 1 && std::isfinite(gmin + smin)) tmax = std::max(tmax, h->rule.ta + 30.0 / (gmin + smin));
+  if (h->L1 > 1 && std::isfinite(gmin + smin) && reac_near)
+    tmax = std::max(tmax, h->rule.ta + 30.0 / (gmin + smin));
+  if ((tmax - h->rule.ta) / h->rule.panel > 4.0e6)
+    throw FmmError(FMM_ERR_UNSUPPORTED, "points too close to an interface: the quadrature tail would exceed 4e6 panels");
   rule_extend(h, tmax, st);
   const int Q = h->rule.Q();
-  for (ReacJob& j : rjobs) {
-    j.sig_off *= Q;
-    double H = j.zt + j.zs;
-    j.Q = h->rule.nodes_to(h->rule.ta + (30.0 + 7.0 * p) / H);
-  }
   h->stats.n_quad_total = Q;
-  // build operators
-  cplx* shift_ops = need<cplx>(ws.m2m_op, std::max<long>(off_shift, 1));
-  cplx* m2l_ops = need<cplx>(ws.m2l_free, std::max<long>(off_m2l, 1));
-  cplx* radial = need<cplx>(ws.m2l_reac, std::max<long>(off_radial, 1));
-  {
-    SepJob* dj = (SepJob*)need<char>(ws.l2l_op, sizeof(SepJob) * std::max<size_t>(1, sep.size() + sep_m2l.size()));
-    std::vector<SepJob> all = sep;
-    size_t n_shift = sep.size();
-    for (SepJob j : sep_m2l) all.push_back(j);
+  long n_classes = 0, t_nodes = 0;
+  if (!sep_shift.empty() || !sep_free.empty()) {
+    std::vector<SepJob> all = sep_shift;
+    all.insert(all.end(), sep_free.begin(), sep_free.end());
+    SepJob* dj = (SepJob*)need<char>(ws.op_tab, sizeof(SepJob) * all.size());
     FMM_CHECK(cudaMemcpyAsync(dj, all.data(), sizeof(SepJob) * all.size(), cudaMemcpyHostToDevice, st));
-    launch_sep_ops(p, dj, (int)n_shift, h->tab.gaunt.as<double>(), shift_ops, st);
-    launch_sep_ops(p, dj + n_shift, (int)sep_m2l.size(), h->tab.gaunt.as<double>(), m2l_ops, st);
+    launch_sep_ops(p, dj, (int)sep_shift.size(), h->tab.gaunt.as<double>(), oc.shift_buf.as<cplx>(), st);
+    launch_sep_ops(p, dj + sep_shift.size(), (int)sep_free.size(), h->tab.gaunt.as<double>(), oc.free_buf.as<cplx>(), st);
     FMM_CHECK(cudaGetLastError());
-    if (!rjobs.empty()) {
-      ReacJob* rj = (ReacJob*)need<char>(ws.out_tmp, sizeof(ReacJob) * rjobs.size());
-      FMM_CHECK(cudaMemcpyAsync(rj, rjobs.data(), sizeof(ReacJob) * rjobs.size(), cudaMemcpyHostToDevice, st));
-      launch_reac_T(p, rj, (int)rjobs.size(), h->rule, radial, st);
-      FMM_CHECK(cudaGetLastError());
-      ExpandJob* dex = (ExpandJob*)need<char>(ws.op_tab, sizeof(ExpandJob) * expand.size());
-      FMM_CHECK(cudaMemcpyAsync(dex, expand.data(), sizeof(ExpandJob) * expand.size(), cudaMemcpyHostToDevice, st));
-      launch_phase_expand(p, dex, (int)expand.size(), radial, m2l_ops, st);
-      FMM_CHECK(cudaGetLastError());
+  }
+  for (Pending& pd : pend) {
+    const Comp& C_ = comps[pd.c];
+    double w = cg[pd.c].h2 / (double)(1 << pd.l);
+    ReacGroup g{};
+    g.l = C_.l; g.lp = C_.lp; g.a = C_.a; g.b = C_.b;
+    g.kl = h->k[C_.l]; g.klp = h->k[C_.lp];
+    g.zt = (pd.jt + 0.5) * w;
+    g.zs = (pd.js + 0.5) * w;
+    g.sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * Q;
+    g.Q = h->rule.nodes_to(h->rule.ta + (30.0 + 7.0 * p) / (g.zt + g.zs));
+    std::vector<double> rho;
+    std::vector<long> offs;
+    for (int r : pd.rs) {
+      rho.push_back(sqrt((double)RHO2[r]) * w);
+      long off = cache_alloc(oc.rad_buf, oc.rad_used, PP, st);
+      offs.push_back(off);
+      oc.rad[std::make_tuple(C_.l, C_.lp, C_.a, C_.b, dbits(w), pd.jt, pd.js, r)] = off;
+      reac_off[((size_t)pd.c * 23 + pd.l) * 40 + (pd.jt * 2 + pd.js) * 10 + r] = off;
     }
-    FMM_CHECK(cudaStreamSynchronize(st));
+    // small per-group argument arrays: stream-ordered uploads from a pinned-free host copy
+    double* drho = need<double>(ws.out_tmp, 16);
+    long* doff = (long*)(drho + 10);
+    std::vector<char> blob(sizeof(double) * 10 + sizeof(long) * 10, 0);
+    memcpy(blob.data(), rho.data(), sizeof(double) * rho.size());
+    memcpy(blob.data() + sizeof(double) * 10, offs.data(), sizeof(long) * offs.size());
+    FMM_CHECK(cudaMemcpyAsync(drho, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
+    launch_reac_group(p, g, h->rule, (int)rho.size(), drho, doff, oc.rad_buf.as<cplx>(), ws.m2l_reac, st);
+    FMM_CHECK(cudaGetLastError());
+    FMM_CHECK(cudaStreamSynchronize(st));     // the argument blob is reused by the next group
+    n_classes += (long)rho.size();
+    t_nodes += (long)g.Q * (long)rho.size();
   }
+  // any still-missing offsets (classes computed by an earlier evaluation)
+  for (int c = 0; c < nc; ++c) {
+    if (comps[c].kind != CK_REAC) continue;
+    for (int l = 2; l <= maxlev; ++l) {
+      double w = cg[c].h2 / (double)(1 << l);
+      for (int g = 0; g < 40; ++g) {
+        size_t idx = ((size_t)c * 23 + l) * 40 + g;
+        if (!used[idx] || reac_off[idx] >= 0) continue;
+        const Comp& C_ = comps[c];
+        reac_off[idx] = oc.rad.at(std::make_tuple(C_.l, C_.lp, C_.a, C_.b, dbits(w), (g / 10) / 2, (g / 10) % 2, g % 10));
+      }
+    }
+  }
+  FMM_CHECK(cudaStreamSynchronize(st));
   h->stats.ms_operators = ms_since(t1);
-  h->stats.n_reac_classes = (long)rjobs.size();
-  h->stats.n_free_ops = (long)sep_m2l.size();
-  {
-    long tq = 0;
-    for (const ReacJob& j : rjobs) tq += j.Q;
-    h->stats.n_reac_T_nodes = tq;
-  }
+  h->stats.n_reac_classes = n_classes;
+  h->stats.n_free_ops = (long)sep_free.size();
+  h->stats.n_reac_T_nodes = t_nodes;
   E.mark(2, st);
   // ---- passes
   auto t2 = Clock::now();
-  CompGeom* dcg = upload(ws.segl, cg, st);   // segl is free after the tree build
-  long* dm2m = nullptr;
+  long* dtabs = nullptr;
   {
     std::vector<long> tabs;
     tabs.insert(tabs.end(), m2m_base.begin(), m2m_base.end());
     tabs.insert(tabs.end(), l2l_base.begin(), l2l_base.end());
     tabs.insert(tabs.end(), m2l_base.begin(), m2l_base.end());
-    dm2m = upload(ws.lvlscan, tabs, st);
+    tabs.insert(tabs.end(), reac_off.begin(), reac_off.end());
+    dtabs = upload(ws.lvlscan, tabs, st);
   }
-  BoxGeom B;
-  B.comp = ws.bcomp.as<int>(); B.lev = ws.blevel.as<int>(); B.sb = ws.bsb.as<int>(); B.se = ws.bse.as<int>();
-  B.tb = ws.btb.as<int>(); B.te = ws.bte.as<int>(); B.parent = ws.bparent.as<int>();
-  B.child0 = ws.bchild0.as<int>(); B.nchild = ws.bnchild.as<int>(); B.coord = ws.bcoord.as<int>();
   cplx* M = need<cplx>(ws.M, (size_t)nb * P);
   cplx* L = need<cplx>(ws.L, (size_t)nb * P);
-  // schedules
   std::vector<int> p2m_leaves, l2p_leaves, near_free, near_reac;
   std::vector<std::vector<int>> m2m_lvl(23), m2l_lvl(23);
   for (int l = 0; l <= maxlev; ++l)
@@ -464,28 +520,27 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
        o_near_reac = push(near_reac);
   std::vector<long> o_m2m(23), o_m2l(23);
   for (int l = 0; l <= maxlev; ++l) { o_m2m[l] = push(m2m_lvl[l]); o_m2l[l] = push(m2l_lvl[l]); }
-  int* dsched = upload(ws.lvlcnt, sched, st);
-  int* err = need<int>(ws.flags, 1);
+  int* dsched = upload(ws.lcnt, sched, st);
   FMM_CHECK(cudaMemsetAsync(err, 0, 4, st));
   // upward pass
   launch_p2m(p, dsched + o_p2m, (int)p2m_leaves.size(), B, dcg, ws.spos.as<double>(), ws.sq.as<cplx>(), M, st);
   for (int l = maxlev; l >= 2; --l)
-    launch_m2m(p, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, dm2m, shift_ops, M, st);
+    launch_m2m(p, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, dtabs, oc.shift_buf.as<cplx>(), M, st);
   FMM_CHECK(cudaGetLastError());
   E.mark(3, st);
   // downward pass
   OpIndex OI;
-  OI.m2l_base = dm2m + 2 * nc * 23;
-  OI.l2l_base = dm2m + nc * 23;
+  OI.l2l_base = dtabs + nc * 23;
+  OI.m2l_base = dtabs + 2 * nc * 23;
+  OI.reac_off = dtabs + 3 * nc * 23;
   OI.cgs = dcg;
-  const int* loff = ws.loff.as<int>();
   for (int l = 2; l <= maxlev; ++l)
     launch_m2l(p, dsched + o_m2l[l], (int)m2l_lvl[l].size(), l >= 3 ? 1 : 0, B, OI, loff, ws.vi.as<int>(),
-               m2l_ops, shift_ops, M, L, err, st);
+               oc.free_buf.as<cplx>(), oc.shift_buf.as<cplx>(), oc.rad_buf.as<cplx>(), M, L, err, st);
   FMM_CHECK(cudaGetLastError());
   E.mark(4, st);
-  cplx* phi = need<cplx>(ws.phi, std::max<long>(1, comps.empty() ? 1 : comps.back().to + comps.back().nt));
   long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;
+  cplx* phi = need<cplx>(ws.phi, std::max<long>(1, NT));
   FMM_CHECK(cudaMemsetAsync(phi, 0, sizeof(cplx) * NT, st));
   launch_l2p(p, dsched + o_l2p, (int)l2p_leaves.size(), B, dcg, ws.tpos.as<double>(), L, phi, st);
   // near field
@@ -514,7 +569,6 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 2, st);
   FMM_CHECK(cudaGetLastError());
   E.mark(7, st);
-  // sum of the components in their fixed order
   for (int c = 0; c < nc; ++c)
     launch_scatter_add(comps[c].nt, ws.tidx.as<int>() + comps[c].to, phi + comps[c].to, out, st);
   if (h->flags & FMM_NORM_PAPER) launch_norm_paper(nt, tgt, medium_of(h), out, st);
@@ -525,7 +579,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaMemcpyAsync(hc, counters, 32, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
-  if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair outside the interface band");
+  if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair without an operator");
   h->stats.ms_eval = ms_since(t2);
   h->stats.gpu_ms_tree = E.ms(0, 1);
   h->stats.gpu_ms_operators = E.ms(1, 2);

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "fmm_math.cuh"
@@ -113,6 +115,23 @@ struct Workspace {
   DevBuf cub_tmp;
 };
 
+// Translation operators kept across evaluations: they depend only on the box
+// width of a level, the wave numbers and (reaction) the layer pair, arrows and
+// the box positions relative to the interface.
+struct OpCache {
+  DevBuf free_buf, shift_buf, rad_buf;
+  long free_used = 0, shift_used = 0, rad_used = 0;      // elements (cplx)
+  std::map<std::pair<uint64_t, uint64_t>, long> free_m2l;              // (k, w) -> 343 slots
+  std::map<std::tuple<uint64_t, uint64_t, int>, long> shift;           // (k, w, kind) -> 8 octants
+  std::map<std::tuple<int, int, int, int, uint64_t, int, int, int>, long> rad;  // (l,l',a,b,w,jt,js,r)
+  void clear() {
+    free_used = shift_used = rad_used = 0;
+    free_m2l.clear();
+    shift.clear();
+    rad.clear();
+  }
+};
+
 struct fmm_layered {
   int L1 = 0;               // number of layers
   std::vector<double> k, d, eps;
@@ -123,6 +142,7 @@ struct fmm_layered {
   Rule rule;
   Tables tab;
   Workspace ws;
+  OpCache cache;
   fmm_stats_t stats{};
   std::string err;
   // state of the last evaluation (for export)
@@ -138,14 +158,12 @@ extern long g_fmm_launches;
 
 // ---- plain-data structures passed to kernels
 struct SepJob { double b[3]; double k; int kind; long out_off; };
-struct ReacJob {
+struct ReacGroup {
   int l, lp, a, b;
   double kl, klp;
-  int Q;                 // nodes used
-  double zt, zs;         // distances of target and image centres from the interface
-  double rho, phi;       // horizontal offset of the class
-  long out_off;          // element offset of the operator (OpT layout)
-  long sig_off;          // offset of sigma^{ab}_{l l'} in the rule's sigma array
+  int Q;                  // quadrature nodes used (near + tail)
+  double zt, zs;          // distances of the target and image box centres from the interface
+  long sig_off;           // sigma^{ab}_{l l'} row in the rule's sigma array
 };
 struct BoxGeom { const int *comp, *lev, *sb, *se, *tb, *te, *parent, *child0, *nchild, *coord; };
 struct CompGeom {
@@ -156,7 +174,12 @@ struct CompGeom {
   int a;
   double dref;
 };
-struct OpIndex { const long* m2l_base; const long* l2l_base; const CompGeom* cgs; };
+struct OpIndex {
+  const long* m2l_base;   // [comp * 23 + level] free space: offset of the 343-slot block
+  const long* l2l_base;   // [comp * 23 + level] offset of the 8 L2L operators
+  const long* reac_off;   // [(comp * 23 + level) * 40 + (jt * 2 + js) * 10 + r] radial reaction operator
+  const CompGeom* cgs;
+};
 struct RuleView {
   const cplx *kr, *coef;   // coef[(l,l',a,b)][q] = (i/4pi) w k_rho sigma / k_lz
   const cplx* kz;          // [L1][Q]
@@ -166,7 +189,7 @@ struct RuleView {
 struct NearComp { int kind, l, lp, a, b; double k; double dref; long coef_off; };
 struct NearBoxes { const int *comp, *lev, *sb, *se, *tb, *te, *parent; const int *uo, *ui, *wo, *wi, *xo, *xi; };
 struct DirectMedium { int L1; double k[FMM_MAXL], d[FMM_MAXL]; };
-struct ExpandJob { long src, dst; double phi; };
+
 
 // medium.cu
 void gauss_legendre_pub(int n, std::vector<double>& x, std::vector<double>& w);

@@ -21,6 +21,7 @@
 //   with z = h^(1) for S and z = j for S^; the Gaunt coefficients
 //   G(n,m;nu,mu;q) = int Y_n^m Y_nu^mu conj(Y_q^{m+mu}) dOmega are computed here by
 //   Gauss-Legendre quadrature in cos(theta) (exact for these polynomials).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -126,94 +127,206 @@ __global__ void k_sep_ops(int p, const SepJob* __restrict__ jobs, const double* 
 }
 
 // ---------------------------------------------------------------- reaction T
-// Per-node factors of the reaction M2L integrand for one component and level:
-//   A[q][i] = i^n s_t P^_n^m(k_lz/k_l) * w k_rho sigma / k_lz
-//   B[q][j] = i^{n'} s_s P^_{n'}^{m'}(k_l'z/k_l')
-// with the vertical exponentials applied per class.
+// For one group (component, level, jt, js) and its nodes q:
+//   near nodes (complex): Ac[q][i] = i^n s_t P^_n^m(k_lz/k_l) c_q e^{i k_lz zt},
+//                         Bc[q][j] = i^{n'} s_s P^_{n'}^{m'}(k_l'z/k_l') e^{i k_l'z zs},
+//   with c_q = w k_rho sigma / k_lz;  T_ij += i^{1+m'-m} Ac J_{m'-m} Bc.
+//   tail nodes (real k_rho = t, k_z = i kappa): P^_n^m(i y) = i^{n-m} R_n^m(y)
+//   with R real (R_n = a y R_{n-1} + b R_{n-2}; R_n^{-m} = R_n^m), c_q = -i w t sigma / kappa_l,
+//   and every factor of i cancels:  T_ij += Ar J_{m'-m} Br with
+//   Ar[q][i] = (-1)^{n+m} s_t R_n^m |c_q| e^{-kappa_l zt}, Br = (-1)^{n'} s_s R_{n'}^{m'} e^{-kappa_l' zs}.
 
 
-// One CTA per (job, row block m): computes the rows with order m of T for all
-// columns.  Shared tiles over the quadrature nodes.
-#define TQ 16
-__global__ void k_reac_T(int p, const ReacJob* __restrict__ jobs, const cplx* __restrict__ kr,
-                         const cplx* __restrict__ w, const cplx* __restrict__ kz, int Qall,
-                         const cplx* __restrict__ sigma, cplx* __restrict__ ops) {
-  const ReacJob jb = jobs[blockIdx.x];
-  const int m = (int)blockIdx.y - p;
+__device__ inline double st_sign(int a, int n, int m) { return (a == AR_UP) ? 1.0 : sgn_pow(n + m); }
+__device__ inline double ss_sign(int a, int n, int m) { return (a == AR_UP) ? sgn_pow(n) : sgn_pow(m); }
+
+// one thread per node: A and B rows
+__global__ void k_reac_nodes(int p, ReacGroup g, int n_near, const cplx* __restrict__ kr, const cplx* __restrict__ w,
+                             const cplx* __restrict__ kz, int Qall, const cplx* __restrict__ sigma,
+                             cplx* __restrict__ Ac, cplx* __restrict__ Bc, double* __restrict__ Ar,
+                             double* __restrict__ Br) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.Q) return;
   const int P = (p + 1) * (p + 1);
-  const int nrow = p + 1 - abs(m);
-  const int DM = 4 * p + 1;
-  extern __shared__ cplx sm[];
-  cplx* As = sm;                       // [TQ][nrow]
-  cplx* Bs = As + TQ * (p + 1);        // [TQ][P]
-  cplx* Js = Bs + TQ * P;              // [TQ][DM]  J_d, d = -2p..2p
-  const int nout = nrow * P;
-  const int per = (nout + blockDim.x - 1) / blockDim.x;
-  cplx acc[8];
-  for (int k = 0; k < 8; ++k) acc[k] = C(0, 0);
-  for (int q0 = 0; q0 < jb.Q; q0 += TQ) {
-    int nq = min(TQ, jb.Q - q0);
-    __syncthreads();
-    // fill tiles: each thread handles nodes
-    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
-      int q = q0 + t;
-      cplx k_r = kr[q];
-      cplx kzl = kz[jb.l * Qall + q], kzp = kz[jb.lp * Qall + q];
-      cplx ph_t[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
-      // target-layer Legendre functions (rows of order m)
-      phat_complex(p, cscale(kzl, 1.0 / jb.kl), cscale(k_r, 1.0 / jb.kl), ph_t);
-      cplx base = cdiv(cmul(cmul(w[q], k_r), sigma[jb.sig_off + q]), kzl);
-      // vertical exponentials Z~: target factor e^{i k_lz zt}, source e^{i k_l'z zs}
-      cplx ez = cexp_(cadd(cmul(C(0, jb.zt), kzl), cmul(C(0, jb.zs), kzp)));
-      base = cmul(base, ez);
-      int am = abs(m);
-      for (int r = 0; r < nrow; ++r) {
-        int n = am + r;
-        cplx v = ph_t[PH(n, am)];
-        if (m < 0 && (am & 1)) v = cneg(v);
-        double st = (jb.a == AR_UP) ? 1.0 : sgn_pow(n + m);
-        v = cscale(cmul(ipow(n), v), st);
-        As[t * (p + 1) + r] = cmul(v, base);
+  cplx kzl = kz[(long)g.l * Qall + q], kzp = kz[(long)g.lp * Qall + q];
+  cplx sg = sigma[g.sig_off + q];
+  if (q < n_near) {
+    cplx k_r = kr[q];
+    cplx c = cdiv(cmul(cmul(w[q], k_r), sg), kzl);
+    cplx et = cexp_(cmul(C(0, g.zt), kzl)), es = cexp_(cmul(C(0, g.zs), kzp));
+    c = cmul(c, et);
+    cplx ph[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
+    phat_complex(p, cscale(kzl, 1.0 / g.kl), cscale(k_r, 1.0 / g.kl), ph);
+    for (int i = 0; i < P; ++i) {
+      int n = (int)floor(sqrt((double)i)), m = i - n * n - n, am = abs(m);
+      cplx v = ph[n * (n + 1) / 2 + am];
+      if (m < 0 && (am & 1)) v = cneg(v);
+      Ac[(long)q * P + i] = cscale(cmul(cmul(ipow(n), v), c), st_sign(g.a, n, m));
+    }
+    phat_complex(p, cscale(kzp, 1.0 / g.klp), cscale(k_r, 1.0 / g.klp), ph);
+    for (int j = 0; j < P; ++j) {
+      int n = (int)floor(sqrt((double)j)), m = j - n * n - n, am = abs(m);
+      cplx v = ph[n * (n + 1) / 2 + am];
+      if (m < 0 && (am & 1)) v = cneg(v);
+      Bc[(long)q * P + j] = cscale(cmul(cmul(ipow(n), v), es), ss_sign(g.a, n, m));
+    }
+  } else {
+    long qt = q - n_near;
+    double t = kr[q].x, kapl = kzl.y, kapp = kzp.y;
+    double cR = w[q].x * t * sg.x / kapl;                 // c = -i cR
+    double et = exp(-kapl * g.zt), es = exp(-kapp * g.zs);
+    double R[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
+    for (int side = 0; side < 2; ++side) {
+      double k = side ? g.klp : g.kl, y = (side ? kapp : kapl) / k, s = t / k;
+      double diag = 0.28209479177387814;
+      for (int m = 0; m <= p; ++m) {
+        if (m > 0) diag *= sqrt((2.0 * m + 1.0) / (2.0 * m)) * s;
+        R[m * (m + 1) / 2 + m] = diag;
+        double r2 = 0.0, r1 = diag;
+        for (int n = m + 1; n <= p; ++n) {
+          double cur = rec_a(n, m) * y * r1 + rec_b(n, m) * r2;
+          R[n * (n + 1) / 2 + m] = cur;
+          r2 = r1;
+          r1 = cur;
+        }
       }
-      phat_complex(p, cscale(kzp, 1.0 / jb.klp), cscale(k_r, 1.0 / jb.klp), ph_t);
-      for (int j = 0; j < P; ++j) {
-        int n = (int)floor(sqrt((double)j)), mm = j - n * n - n, am2 = abs(mm);
-        cplx v = ph_t[PH(n, am2)];
-        if (mm < 0 && (am2 & 1)) v = cneg(v);
-        double ss = (jb.a == AR_UP) ? sgn_pow(n) : sgn_pow(mm);
-        Bs[t * P + j] = cscale(cmul(ipow(n), v), ss);
-      }
-      cplx Jv[2 * (2 * FMM_MAXP) + 1];
-      besselJ_all(2 * p, cscale(k_r, jb.rho), Jv);
-      for (int d = 0; d <= 2 * p; ++d) {
-        Js[t * DM + 2 * p + d] = Jv[d];
-        Js[t * DM + 2 * p - d] = cscale(Jv[d], sgn_pow(d));
+      for (int i = 0; i < P; ++i) {
+        // P^_n^m(i y) = i^{n-m} R_n^{|m|}(y) for either sign of m (the factor
+        // (-1)^m of P^_n^{-m} is contained in i^{n-m})
+        int n = (int)floor(sqrt((double)i)), m = i - n * n - n, am = abs(m);
+        double v = R[n * (n + 1) / 2 + am];
+        if (side == 0) Ar[qt * P + i] = sgn_pow(n + m) * st_sign(g.a, n, m) * v * cR * et;
+        else Br[qt * P + i] = sgn_pow(n) * ss_sign(g.a, n, m) * v * es;
       }
     }
+  }
+}
+
+// J_d(k_rho rho_r), d = 0..2p, for every node and radial class r
+__global__ void k_reac_bessel(int p, int Q, int n_near, int nr, const double* __restrict__ rho,
+                              const cplx* __restrict__ kr, cplx* __restrict__ Jc, double* __restrict__ Jr) {
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)Q * nr) return;
+  int q = e % Q, r = e / Q;
+  const int D = 2 * p + 1;
+  if (q < n_near) {
+    cplx J[2 * (2 * FMM_MAXP) + 1];
+    besselJ_all(2 * p, cscale(kr[q], rho[r]), J);
+    for (int d = 0; d < D; ++d) Jc[((long)r * n_near + q) * D + d] = J[d];
+  } else {
+    double x = kr[q].x * rho[r];
+    long base = ((long)r * (Q - n_near) + (q - n_near)) * D;
+    if (x > 2.0 * p + 2.0) {
+      // upward recurrence is stable for d < x
+      double j0v = j0(x), j1v = j1(x);
+      Jr[base] = j0v;
+      if (D > 1) Jr[base + 1] = j1v;
+      for (int d = 1; d + 1 < D; ++d) {
+        double j2 = 2.0 * d / x * j1v - j0v;
+        j0v = j1v;
+        j1v = j2;
+        Jr[base + d + 1] = j2;
+      }
+    } else {
+      cplx J[2 * (2 * FMM_MAXP) + 1];
+      besselJ_all(2 * p, C(x, 0.0), J);
+      for (int d = 0; d < D; ++d) Jr[base + d] = J[d].x;
+    }
+  }
+}
+
+// T_rad[r] (OpT layout [j][i]) for one group: CTA per (radial class, m block).
+#define TQR 32
+__global__ void k_reac_contract(int p, int Q, int n_near, const cplx* __restrict__ Ac, const cplx* __restrict__ Bc,
+                                const double* __restrict__ Ar, const double* __restrict__ Br,
+                                const cplx* __restrict__ Jc, const double* __restrict__ Jr,
+                                const long* __restrict__ out_off, cplx* __restrict__ ops) {
+  const int r = blockIdx.x;
+  const int m = (int)blockIdx.y - p;
+  const int P = (p + 1) * (p + 1);
+  const int D = 2 * p + 1;
+  const int am = abs(m), nrow = p + 1 - am;
+  const int nout = nrow * P;
+  extern __shared__ double smr[];
+  // tail tiles: A[TQR][nrow], B[TQR][P], J[TQR][D]; near tiles reuse the space as complex
+  double* sA = smr;
+  double* sB = sA + 2 * TQR * (FMM_MAXP + 1);
+  double* sJ = sB + 2 * TQR * P;
+  const int per = (nout + blockDim.x - 1) / blockDim.x;
+  double accr[8], acci[8];
+  int oi[8], oj[8], od[8];
+  for (int k = 0; k < 8; ++k) {
+    accr[k] = acci[k] = 0.0;
+    int o = threadIdx.x + k * blockDim.x;
+    oi[k] = o / P;
+    oj[k] = o % P;
+    int n2 = (int)floor(sqrt((double)oj[k])), mm = oj[k] - n2 * n2 - n2;
+    od[k] = mm - m;     // may be negative
+  }
+  // near nodes (complex)
+  cplx* cA = (cplx*)sA;
+  cplx* cB = (cplx*)sB;
+  cplx* cJ = (cplx*)sJ;
+  for (int q0 = 0; q0 < n_near; q0 += TQR / 2) {
+    int nq = min(TQR / 2, n_near - q0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * nrow; e += blockDim.x) {
+      int t = e / nrow, rr = e % nrow;
+      int n = am + rr;
+      cA[t * nrow + rr] = Ac[(long)(q0 + t) * P + n * n + n + m];
+    }
+    for (int e = threadIdx.x; e < nq * P; e += blockDim.x) cB[e] = Bc[(long)q0 * P + e];
+    for (int e = threadIdx.x; e < nq * D; e += blockDim.x) cJ[e] = Jc[((long)r * n_near + q0) * D + e];
     __syncthreads();
     for (int k = 0; k < per && k < 8; ++k) {
       int o = threadIdx.x + k * blockDim.x;
       if (o >= nout) break;
-      int r = o / P, j = o % P;
-      int n2 = (int)floor(sqrt((double)j)), mm = j - n2 * n2 - n2;
-      int dd = mm - m + 2 * p;
-      cplx a = acc[k];
-      for (int t = 0; t < nq; ++t) cfma(a, cmul(As[t * (p + 1) + r], Js[t * DM + dd]), Bs[t * P + j]);
-      acc[k] = a;
+      int d = od[k], ad = abs(d);
+      double sgnd = (d < 0 && (ad & 1)) ? -1.0 : 1.0;
+      cplx a = C(accr[k], acci[k]);
+      for (int t = 0; t < nq; ++t) {
+        cplx jv = cscale(cJ[t * D + ad], sgnd);
+        cfma(a, cmul(cA[t * nrow + oi[k]], jv), cB[t * P + oj[k]]);
+      }
+      accr[k] = a.x;
+      acci[k] = a.y;
+    }
+  }
+  // multiply the near part by i^{1+d}
+  for (int k = 0; k < per && k < 8; ++k) {
+    cplx v = cmul(ipow(1 + od[k]), C(accr[k], acci[k]));
+    accr[k] = v.x;
+    acci[k] = v.y;
+  }
+  // tail nodes (real)
+  const int Qt = Q - n_near;
+  for (int q0 = 0; q0 < Qt; q0 += TQR) {
+    int nq = min(TQR, Qt - q0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * nrow; e += blockDim.x) {
+      int t = e / nrow, rr = e % nrow;
+      int n = am + rr;
+      sA[t * nrow + rr] = Ar[(long)(q0 + t) * P + n * n + n + m];
+    }
+    for (int e = threadIdx.x; e < nq * P; e += blockDim.x) sB[e] = Br[(long)q0 * P + e];
+    for (int e = threadIdx.x; e < nq * D; e += blockDim.x) sJ[e] = Jr[((long)r * Qt + q0) * D + e];
+    __syncthreads();
+    for (int k = 0; k < per && k < 8; ++k) {
+      int o = threadIdx.x + k * blockDim.x;
+      if (o >= nout) break;
+      int d = od[k], ad = abs(d);
+      double sgnd = (d < 0 && (ad & 1)) ? -1.0 : 1.0;
+      double a = 0.0;
+      for (int t = 0; t < nq; ++t) a += sA[t * nrow + oi[k]] * sJ[t * D + ad] * sB[t * P + oj[k]];
+      accr[k] += sgnd * a;
     }
   }
   for (int k = 0; k < per && k < 8; ++k) {
     int o = threadIdx.x + k * blockDim.x;
     if (o >= nout) break;
-    int r = o / P, j = o % P;
-    int n = abs(m) + r;
-    int i = NM(n, m);
-    int n2 = (int)floor(sqrt((double)j)), mm = j - n2 * n2 - n2;
-    int d = mm - m;
-    double s, c;
-    sincos(d * jb.phi, &s, &c);
-    cplx pref = cmul(ipow(1 + d), C(c, s));
-    ops[jb.out_off + (long)j * P + i] = cmul(pref, acc[k]);
+    int n = am + oi[k];
+    int i = n * n + n + m;
+    ops[out_off[r] + (long)oj[k] * P + i] = C(accr[k], acci[k]);
   }
 }
 
@@ -323,25 +436,21 @@ __global__ void k_m2m(int p, const int* __restrict__ boxes, BoxGeom B, const lon
 // expansion) + sum_{S in V(T)} OpM2L(T, S) M_S.
 
 
-__device__ inline long m2l_slot(const CompGeom& cg, int level, const int* ct, const int* cs, int* err) {
-  int dx = ct[0] - cs[0], dy = ct[1] - cs[1], dz = ct[2] - cs[2];
-  if (cg.kind == CK_FREE) return ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
-  int half = 1 << (level - 1);
-  int jt, js;
-  if (cg.a == AR_UP) { jt = ct[2] - half; js = half - 1 - cs[2]; }
-  else { jt = half - 1 - ct[2]; js = cs[2] - half; }
-  if (jt < 0 || jt > 1 || js < 0 || js > 1) { atomicOr(err, 8); return 0; }
-  return ((jt * 2 + js) * 7 + (dy + 3)) * 7 + (dx + 3);
-}
-
 __global__ void k_m2l(int p, const int* __restrict__ boxes, int with_l2l, BoxGeom B, OpIndex OI,
                       const int* __restrict__ voff, const int* __restrict__ vidx,
-                      const cplx* __restrict__ m2l_ops, const cplx* __restrict__ l2l_ops,
-                      const cplx* __restrict__ M, cplx* __restrict__ L, int* __restrict__ err) {
+                      const cplx* __restrict__ free_ops, const cplx* __restrict__ l2l_ops,
+                      const cplx* __restrict__ reac_ops, const cplx* __restrict__ M, cplx* __restrict__ L,
+                      int* __restrict__ err) {
   int T = boxes[blockIdx.x];
   const int P = (p + 1) * (p + 1);
   extern __shared__ cplx xs[];
   cplx acc[4] = {C(0, 0), C(0, 0), C(0, 0), C(0, 0)};
+  int mi[4];
+  for (int kk = 0; kk < 4; ++kk) {
+    int i = threadIdx.x + kk * blockDim.x;
+    int n = (int)floor(sqrt((double)i));
+    mi[kk] = i - n * n - n;
+  }
   int comp = B.comp[T], lev = B.lev[T];
   const CompGeom cg = OI.cgs[comp];
   if (with_l2l) {
@@ -358,20 +467,58 @@ __global__ void k_m2l(int p, const int* __restrict__ boxes, int with_l2l, BoxGeo
       acc[kk] = a;
     }
   }
-  long base = OI.m2l_base[comp * 23 + lev];
+  const int* ct = B.coord + 3 * T;
   for (int e = voff[T]; e < voff[T + 1]; ++e) {
     int S = vidx[e];
+    const int* cs = B.coord + 3 * S;
+    int dx = ct[0] - cs[0], dy = ct[1] - cs[1], dz = ct[2] - cs[2];
+    const cplx* op;
+    double phi = 0.0;
+    bool reac = cg.kind == CK_REAC;
+    if (!reac) {
+      long slot = ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
+      op = free_ops + OI.m2l_base[comp * 23 + lev] + slot * P * P;
+    } else {
+      int half = 1 << (lev - 1);
+      int jt, js;
+      if (cg.a == AR_UP) { jt = ct[2] - half; js = half - 1 - cs[2]; }
+      else { jt = half - 1 - ct[2]; js = cs[2] - half; }
+      int r2 = dx * dx + dy * dy, r = -1;
+      const int tab[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+      for (int k = 0; k < 10; ++k) if (tab[k] == r2) r = k;
+      long off = -1;
+      if (jt >= 0 && jt <= 1 && js >= 0 && js <= 1 && r >= 0)
+        off = OI.reac_off[((long)comp * 23 + lev) * 40 + (jt * 2 + js) * 10 + r];
+      if (off < 0) {
+        if (threadIdx.x == 0) atomicOr(err, 8);
+        continue;
+      }
+      op = reac_ops + off;
+      phi = atan2((double)dy, (double)dx);
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < P; i += blockDim.x) xs[i] = M[(long)S * P + i];
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+      cplx v = M[(long)S * P + j];
+      if (reac) {
+        int n = (int)floor(sqrt((double)j)), m = j - n * n - n;
+        double sn, cn;
+        sincos(m * phi, &sn, &cn);
+        v = cmul(v, C(cn, sn));
+      }
+      xs[j] = v;
+    }
     __syncthreads();
-    long slot = m2l_slot(cg, lev, B.coord + 3 * T, B.coord + 3 * S, err);
-    const cplx* op = m2l_ops + base + slot * P * P;
     for (int kk = 0; kk < 4; ++kk) {
       int i = threadIdx.x + kk * blockDim.x;
       if (i >= P) break;
-      cplx a = acc[kk];
+      cplx a = C(0, 0);
       for (int j = 0; j < P; ++j) cfma(a, op[(long)j * P + i], xs[j]);
-      acc[kk] = a;
+      if (reac) {
+        double sn, cn;
+        sincos(mi[kk] * phi, &sn, &cn);
+        a = cmul(a, C(cn, -sn));
+      }
+      acc[kk] = cadd(acc[kk], a);
     }
   }
   for (int kk = 0; kk < 4; ++kk) {
@@ -381,22 +528,29 @@ __global__ void k_m2l(int p, const int* __restrict__ boxes, int with_l2l, BoxGeo
   }
 }
 
-// Expand radial reaction integrals (phi = 0) into slots with e^{i (m'-m) phi}.
-__global__ void k_phase_expand(int p, const ExpandJob* __restrict__ jobs, const cplx* __restrict__ srcb,
-                               cplx* __restrict__ dstb) {
-  const int P = (p + 1) * (p + 1);
-  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (e >= (long)P * P) return;
-  const ExpandJob jb = jobs[blockIdx.y];
-  const cplx* src = srcb + jb.src;
-  cplx* dst = dstb + jb.dst;
-  double phi = jb.phi;
-  int j = e / P, i = e % P;
-  int ni = (int)floor(sqrt((double)i)), mi = i - ni * ni - ni;
-  int nj = (int)floor(sqrt((double)j)), mj = j - nj * nj - nj;
-  double s, c;
-  sincos((mj - mi) * phi, &s, &c);
-  dst[e] = cmul(src[e], C(c, s));
+// Mark the reaction M2L classes used by the V lists:
+// used[(comp * 23 + level) * 40 + (jt * 2 + js) * 10 + r] = 1.
+__global__ void k_mark_reac(int nb, BoxGeom B, const CompGeom* __restrict__ cgs, const int* __restrict__ voff,
+                            const int* __restrict__ vidx, unsigned char* __restrict__ used, int* __restrict__ err) {
+  int T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= nb) return;
+  int comp = B.comp[T];
+  if (cgs[comp].kind != CK_REAC) return;
+  int lev = B.lev[T];
+  const int* ct = B.coord + 3 * T;
+  const int tab[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
+  for (int e = voff[T]; e < voff[T + 1]; ++e) {
+    const int* cs = B.coord + 3 * vidx[e];
+    int dx = ct[0] - cs[0], dy = ct[1] - cs[1];
+    int half = 1 << (lev - 1);
+    int jt, js;
+    if (cgs[comp].a == AR_UP) { jt = ct[2] - half; js = half - 1 - cs[2]; }
+    else { jt = half - 1 - ct[2]; js = cs[2] - half; }
+    int r = -1;
+    for (int k = 0; k < 10; ++k) if (tab[k] == dx * dx + dy * dy) r = k;
+    if (jt < 0 || jt > 1 || js < 0 || js > 1 || r < 0) { atomicOr(err, 8); continue; }
+    used[((long)comp * 23 + lev) * 40 + (jt * 2 + js) * 10 + r] = 1;
+  }
 }
 
 // ---------------------------------------------------------------- L2P
@@ -448,16 +602,32 @@ void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx*
   if (njobs) LAUNCH(k_sep_ops<<<njobs, 256, 0, st>>>(p, jobs, G, ops));
 }
 
-void launch_reac_T(int p, const ReacJob* jobs, int njobs, const Rule& R, cplx* ops, cudaStream_t st) {
-  if (!njobs) return;
-  int P = (p + 1) * (p + 1);
-  size_t smem = sizeof(cplx) * (TQ * (p + 1) + TQ * P + TQ * (4 * p + 1));
-  dim3 grid(njobs, 2 * p + 1);
+// Radial reaction M2L matrices of one group for nr radial classes.
+void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const double* d_rho, const long* d_out_off,
+                       cplx* ops, DevBuf& scratch, cudaStream_t st) {
+  const int P = (p + 1) * (p + 1);
+  const int D = 2 * p + 1;
+  const int nn = std::min(R.n_near, g.Q), Qt = g.Q - nn;
+  size_t bytes = sizeof(cplx) * 2 * (size_t)nn * P + sizeof(double) * 2 * (size_t)Qt * P +
+                 sizeof(cplx) * (size_t)nr * nn * D + sizeof(double) * (size_t)nr * Qt * D + 1024;
+  scratch.ensure(bytes);
+  char* base = (char*)scratch.ptr;
+  cplx* Ac = (cplx*)base;
+  cplx* Bc = Ac + (size_t)nn * P;
+  double* Ar = (double*)(Bc + (size_t)nn * P);
+  double* Br = Ar + (size_t)Qt * P;
+  cplx* Jc = (cplx*)(Br + (size_t)Qt * P);
+  double* Jr = (double*)(Jc + (size_t)nr * nn * D);
+  LAUNCH(k_reac_nodes<<<(g.Q + 127) / 128, 128, 0, st>>>(p, g, nn, R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(),
+                                                          R.Q(), R.sigma.as<cplx>(), Ac, Bc, Ar, Br));
+  long ne = (long)g.Q * nr;
+  LAUNCH(k_reac_bessel<<<(ne + 127) / 128, 128, 0, st>>>(p, g.Q, nn, nr, d_rho, R.kr.as<cplx>(), Jc, Jr));
+  size_t smem = sizeof(double) * (2 * TQR * (FMM_MAXP + 1) + 2 * TQR * P + 2 * TQR * D);
+  cudaFuncSetAttribute(k_reac_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int threads = 256;
   while ((p + 1) * P > 8 * threads && threads < 1024) threads *= 2;
-  cudaFuncSetAttribute(k_reac_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  LAUNCH(k_reac_T<<<grid, threads, smem, st>>>(p, jobs, R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(), R.Q(),
-                                        R.sigma.as<cplx>(), ops));
+  dim3 grid(nr, 2 * p + 1);
+  LAUNCH(k_reac_contract<<<grid, threads, smem, st>>>(p, g.Q, nn, Ac, Bc, Ar, Br, Jc, Jr, d_out_off, ops));
 }
 
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
@@ -481,17 +651,15 @@ void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, 
 }
 
 void launch_m2l(int p, const int* boxes, int n, int with_l2l, BoxGeom B, OpIndex OI, const int* voff,
-                const int* vidx, const cplx* m2l_ops, const cplx* l2l_ops, const cplx* M, cplx* L, int* err,
-                cudaStream_t st) {
+                const int* vidx, const cplx* free_ops, const cplx* l2l_ops, const cplx* reac_ops, const cplx* M,
+                cplx* L, int* err, cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  if (n) LAUNCH(k_m2l<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, with_l2l, B, OI, voff, vidx, m2l_ops, l2l_ops, M, L, err));
+  if (n) LAUNCH(k_m2l<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, with_l2l, B, OI, voff, vidx, free_ops, l2l_ops,
+                                                        reac_ops, M, L, err));
 }
 
-void launch_phase_expand(int p, const ExpandJob* jobs, int njobs, const cplx* src, cplx* dst, cudaStream_t st) {
-  long PP = (long)(p + 1) * (p + 1) * (p + 1) * (p + 1);
-  for (int j0 = 0; j0 < njobs; j0 += 60000) {
-    int nj = njobs - j0 < 60000 ? njobs - j0 : 60000;
-    dim3 grid((unsigned)((PP + 255) / 256), nj);
-    LAUNCH(k_phase_expand<<<grid, 256, 0, st>>>(p, jobs + j0, src, dst));
-  }
+void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
+                      int* err, cudaStream_t st) {
+  if (nb) LAUNCH(k_mark_reac<<<(nb + 127) / 128, 128, 0, st>>>(nb, B, cgs, voff, vidx, used, err));
 }
+

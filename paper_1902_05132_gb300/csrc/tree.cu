@@ -22,7 +22,11 @@
 //    the other half; bits interleaved x lowest.
 //  * stable sort by (key, position in the component's list).
 //  * a box of level l < 21 is refined when it holds more than `leaf` sources
-//    or more than `leaf` targets; empty children are dropped.
+//    or more than `leaf` targets, or, in a reaction tree, when it touches the
+//    interface (the root's mid-plane) and holds any point; empty children are
+//    dropped.  The second rule keeps every target leaf at least one box away
+//    from every image leaf, so reaction components are evaluated entirely by
+//    M2L unless points lie within 2^-21 root widths of the interface.
 //  * lists of a target box T (boxes with sources only, closed boxes touching
 //    = adjacent): V(T) children of the parent's colleagues not adjacent to T;
 //    for leaf T, U(T) source leaves adjacent to T (T included) and W(T)
@@ -200,16 +204,29 @@ __device__ inline int lower_bound_u64(const unsigned long long* a, int lo, int h
   return lo;
 }
 
+__device__ inline bool refine_box(int level, int leaf, int ns, int nt, bool reac, int iz) {
+  if (level >= 21) return false;
+  if (ns > leaf || nt > leaf) return true;
+  if (reac && ns + nt > 0) {
+    if (level == 0) return true;
+    int half = 1 << (level - 1);
+    if (iz == half - 1 || iz == half) return true;
+  }
+  return false;
+}
+
 __global__ void k_count_children(int lb, int le, int level, int leaf, const int* __restrict__ sb,
                                  const int* __restrict__ se, const int* __restrict__ tb,
                                  const int* __restrict__ te, const unsigned long long* __restrict__ prefix,
                                  const unsigned long long* __restrict__ skey,
-                                 const unsigned long long* __restrict__ tkey, int* __restrict__ nchild) {
+                                 const unsigned long long* __restrict__ tkey, int* __restrict__ nchild,
+                                 const int* __restrict__ comp, const int* __restrict__ comp_kind,
+                                 const int* __restrict__ coord) {
   int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= le) return;
   int ns = se[b] - sb[b], nt = te[b] - tb[b];
   int cnt = 0;
-  if ((ns > leaf || nt > leaf) && level < 21) {
+  if (refine_box(level, leaf, ns, nt, comp_kind[comp[b]] == CK_REAC, coord[3 * b + 2])) {
     int shift = 3 * (21 - (level + 1));
     for (int o = 0; o < 8; ++o) {
       unsigned long long cp = (prefix[b] << 3) | o;
@@ -696,6 +713,10 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     FMM_CHECK(cudaMemcpyAsync(ws.bparent.ptr, par.data(), 4 * nc, cudaMemcpyHostToDevice, st));
     FMM_CHECK(cudaMemcpyAsync(ws.bcoord.ptr, coord.data(), 12 * nc, cudaMemcpyHostToDevice, st));
   }
+  std::vector<int> kinds(nc);
+  for (int ci = 0; ci < nc; ++ci) kinds[ci] = comps[ci].kind;
+  int* dkind = need<int>(ws.ltmp, nc);
+  FMM_CHECK(cudaMemcpyAsync(dkind, kinds.data(), 4 * nc, cudaMemcpyHostToDevice, st));
   std::vector<int>& lvl = h->lvl_begin;
   lvl.assign(1, 0);
   lvl.push_back(nc);
@@ -708,7 +729,7 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     int* scn = need<int>(ws.lvlscan, n + 1);
     LAUNCH(k_count_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, h->leaf, ws.bsb.as<int>(), ws.bse.as<int>(),
                                                       ws.btb.as<int>(), ws.bte.as<int>(), ws.bprefix.as<unsigned long long>(),
-                                                      skey, tkey, cntl));
+                                                      skey, tkey, cntl, ws.bcomp.as<int>(), dkind, ws.bcoord.as<int>()));
     exclusive_scan(ws, cntl, scn, n, st);
     int last_cnt = 0, last_scan = 0;
     FMM_CHECK(cudaMemcpyAsync(&last_cnt, cntl + n - 1, 4, cudaMemcpyDeviceToHost, st));
