@@ -75,6 +75,7 @@ typedef struct {
   long   n_reac_classes;   /* reaction M2L radial integrals computed         */
   long   n_free_ops;       /* free-space translation operators built         */
   long   n_reac_T_nodes;   /* quadrature nodes summed over those integrals   */
+  long   n_v_pairs_reac;   /* ... of n_v_pairs, in reaction components        */
   long   n_launches;       /* kernels of this library launched by the last
                               evaluation (launches inside CUB's sort and scan
                               calls not included)                            */

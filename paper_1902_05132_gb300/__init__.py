@@ -42,7 +42,7 @@ class Stats(ctypes.Structure):
                 ("n_reac_pairs", ctypes.c_long), ("n_reac_nodes", ctypes.c_long),
                 ("n_reac_tail_nodes", ctypes.c_long), ("n_reac_classes", ctypes.c_long),
                 ("n_free_ops", ctypes.c_long), ("n_reac_T_nodes", ctypes.c_long),
-                ("n_launches", ctypes.c_long)]
+                ("n_v_pairs_reac", ctypes.c_long), ("n_launches", ctypes.c_long)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",

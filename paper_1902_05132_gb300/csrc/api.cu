@@ -18,9 +18,11 @@ void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs,
                 const cplx* sq, cplx* M, cudaStream_t st);
 void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, const cplx* ops, cplx* M,
                 cudaStream_t st);
-void launch_m2l(int p, const int* boxes, int n, int with_l2l, BoxGeom B, OpIndex OI, const int* voff,
-                const int* vidx, const cplx* free_ops, const cplx* l2l_ops, const cplx* reac_ops, const cplx* M,
-                cplx* L, int* err, cudaStream_t st);
+void launch_reac_split(int p, const cplx* full, cplx* out, cudaStream_t st);
+void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
+                  const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
+                  const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
+                  const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st);
 void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
                       int* err, cudaStream_t st);
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
@@ -79,6 +81,15 @@ static void create_impl(fmm_layered* h) {
   double* dw = need<double>(tmpw, wg.size());
   launch_gaunt(p, xg, wg, G, dx, dw, 0);
   FMM_CHECK(cudaGetLastError());
+  // e^{i m phi} for the 49 horizontal offsets of reaction M2L pairs
+  std::vector<cplx> ph(49 * (2 * p + 1));
+  for (int dy = -3; dy <= 3; ++dy)
+    for (int dx = -3; dx <= 3; ++dx) {
+      double phi = atan2((double)dy, (double)dx);
+      for (int m = -p; m <= p; ++m)
+        ph[((dy + 3) * 7 + (dx + 3)) * (2 * p + 1) + (m + p)] = C(cos(m * phi), sin(m * phi));
+    }
+  upload(h->tab.phase, ph, 0);
   FMM_CHECK(cudaStreamSynchronize(0));
   tmpx.release();
   tmpw.release();
@@ -133,7 +144,7 @@ extern "C" int fmm_layered_create(int n_layers, const double* k, const double* i
 extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   if (!h) return;
   DevBuf* all[] = {&h->d_k, &h->d_d, &h->d_eps, &h->rule.kr, &h->rule.w, &h->rule.kz, &h->rule.sigma,
-                   &h->tab.gaunt};
+                   &h->tab.gaunt, &h->tab.phase};
   for (DevBuf* b : all) b->release();
   Workspace& ws = h->ws;
   DevBuf* wsb[] = {&ws.slayer, &ws.tlayer, &ws.sorder, &ws.torder, &ws.iota, &ws.ltmp, &ws.counts, &ws.bbox,
@@ -145,6 +156,8 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
                    &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
                    &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.cub_tmp};
   for (DevBuf* b : wsb) b->release();
+  DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat};
+  for (DevBuf* b : gb) b->release();
   h->cache.free_buf.release();
   h->cache.shift_buf.release();
   h->cache.rad_buf.release();
@@ -306,6 +319,12 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   if (herr0) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair outside the interface band");
   const int* uo = lo_all.data() + (nb + 1);
   h->stats.n_u_pairs = uo[nb];
+  {
+    long vr = 0;
+    for (int b = 0; b < nb; ++b)
+      if (comps[bcomp[b]].kind == CK_REAC) vr += lo_all[b + 1] - lo_all[b];
+    h->stats.n_v_pairs_reac = vr;
+  }
   // does any reaction component need near-field (direct) interactions?
   bool reac_near = false;
   for (int b = 0; b < nb && !reac_near; ++b) {
@@ -445,22 +464,29 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     g.sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * Q;
     g.Q = h->rule.nodes_to(h->rule.ta + (30.0 + 7.0 * p) / (g.zt + g.zs));
     std::vector<double> rho;
-    std::vector<long> offs;
-    for (int r : pd.rs) {
+    std::vector<long> offs, split_offs;
+    const long npp = (long)(p + 1) * (p + 2) / 2, nmm = (long)p * (p + 1) / 2;
+    const long split_elems = npp * npp + nmm * nmm;
+    for (size_t k = 0; k < pd.rs.size(); ++k) {
+      int r = pd.rs[k];
       rho.push_back(sqrt((double)RHO2[r]) * w);
-      long off = cache_alloc(oc.rad_buf, oc.rad_used, PP, st);
-      offs.push_back(off);
+      offs.push_back((long)k * PP);                 // full radial matrix in scratch
+      long off = cache_alloc(oc.rad_buf, oc.rad_used, split_elems, st);
+      split_offs.push_back(off);
       oc.rad[std::make_tuple(C_.l, C_.lp, C_.a, C_.b, dbits(w), pd.jt, pd.js, r)] = off;
       reac_off[((size_t)pd.c * 23 + pd.l) * 40 + (pd.jt * 2 + pd.js) * 10 + r] = off;
     }
+    cplx* full = need<cplx>(ws.out_tmp, (size_t)PP * 10 + 64);
     // small per-group argument arrays: stream-ordered uploads from a pinned-free host copy
-    double* drho = need<double>(ws.out_tmp, 16);
+    double* drho = (double*)(full + (size_t)PP * 10);
     long* doff = (long*)(drho + 10);
     std::vector<char> blob(sizeof(double) * 10 + sizeof(long) * 10, 0);
     memcpy(blob.data(), rho.data(), sizeof(double) * rho.size());
     memcpy(blob.data() + sizeof(double) * 10, offs.data(), sizeof(long) * offs.size());
     FMM_CHECK(cudaMemcpyAsync(drho, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
-    launch_reac_group(p, g, h->rule, (int)rho.size(), drho, doff, oc.rad_buf.as<cplx>(), ws.m2l_reac, st);
+    launch_reac_group(p, g, h->rule, (int)rho.size(), drho, doff, full, ws.m2l_reac, st);
+    for (size_t k = 0; k < rho.size(); ++k)
+      launch_reac_split(p, full + offs[k], oc.rad_buf.as<cplx>() + split_offs[k], st);
     FMM_CHECK(cudaGetLastError());
     FMM_CHECK(cudaStreamSynchronize(st));     // the argument blob is reused by the next group
     n_classes += (long)rho.size();
@@ -533,10 +559,10 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   OI.l2l_base = dtabs + nc * 23;
   OI.m2l_base = dtabs + 2 * nc * 23;
   OI.reac_off = dtabs + 3 * nc * 23;
+  OI.phase = h->tab.phase.as<cplx>();
   OI.cgs = dcg;
-  for (int l = 2; l <= maxlev; ++l)
-    launch_m2l(p, dsched + o_m2l[l], (int)m2l_lvl[l].size(), l >= 3 ? 1 : 0, B, OI, loff, ws.vi.as<int>(),
-               oc.free_buf.as<cplx>(), oc.shift_buf.as<cplx>(), oc.rad_buf.as<cplx>(), M, L, err, st);
+  run_m2l_gemm(h, nb, (long)lo_all[nb], m2l_lvl, dsched, o_m2l, maxlev, B, OI, loff, ws.vi.as<int>(),
+               oc.free_buf.as<cplx>(), oc.rad_buf.as<cplx>(), oc.shift_buf.as<cplx>(), M, L, err, st);
   FMM_CHECK(cudaGetLastError());
   E.mark(4, st);
   long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;

@@ -91,6 +91,7 @@ struct Rule {
 
 struct Tables {             // expansion-order dependent tables built at create
   DevBuf gaunt;             // double [P][P][2p+1], G(n,m; nu,-mu; q)
+  DevBuf phase;             // cplx [49][2p+1], azimuthal phases of the reaction M2L offsets
 };
 
 struct Workspace {
@@ -111,6 +112,8 @@ struct Workspace {
   // operators
   DevBuf m2l_free, m2m_op, l2l_op, m2l_reac, op_tab;
   DevBuf phi;           // per component-target results (sorted order)
+  // M2L as batched GEMMs
+  DevBuf g_owner, g_keys, g_vals, g_inv, g_Y, g_Z, g_runs, g_bat;
   DevBuf out_tmp;
   DevBuf cub_tmp;
 };
@@ -178,6 +181,7 @@ struct OpIndex {
   const long* m2l_base;   // [comp * 23 + level] free space: offset of the 343-slot block
   const long* l2l_base;   // [comp * 23 + level] offset of the 8 L2L operators
   const long* reac_off;   // [(comp * 23 + level) * 40 + (jt * 2 + js) * 10 + r] radial reaction operator
+  const cplx* phase;      // [(dy + 3) * 7 + (dx + 3)][m + p] = e^{i m atan2(dy, dx)}
   const CompGeom* cgs;
 };
 struct RuleView {

@@ -27,10 +27,12 @@ __host__ __device__ inline cplx cdiv(cplx a, cplx b) {
   double d = bx * bx + by * by;
   return C((a.x * bx + a.y * by) / (d * s), (a.y * bx - a.x * by) / (d * s));
 }
-// acc += a * b
+// acc += a * b as four fused multiply-adds (no separate multiply or add)
 __host__ __device__ inline void cfma(cplx& acc, cplx a, cplx b) {
-  acc.x += a.x * b.x - a.y * b.y;
-  acc.y += a.x * b.y + a.y * b.x;
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
 }
 // i^e for integer e
 __host__ __device__ inline cplx ipow(int e) {

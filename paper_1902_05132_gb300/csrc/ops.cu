@@ -330,6 +330,60 @@ __global__ void k_reac_contract(int p, int Q, int n_near, const cplx* __restrict
   }
 }
 
+// Symmetric split of a radial reaction operator.  With the signed reflection
+// (R x)_{n,m} = (-1)^m x_{n,-m}, the radial integral satisfies
+// I(n,-m; n',-m') = (-1)^{m+m'} I(n,m; n',m'), so I commutes with R and is block
+// diagonal in the orthonormal basis
+//   plus:  e_{n,0};  (e_{n,m} + (-1)^m e_{n,-m}) / sqrt2   (m > 0), index n(n+1)/2 + m
+//   minus: (e_{n,m} - (-1)^m e_{n,-m}) / sqrt2              (m > 0), index n(n-1)/2 + m - 1
+// Output: Ip [b][a] (np x np) followed by Im [b][a] (nm x nm), input-major.
+__device__ inline int basis_terms(int p, int a, bool plus, int* idx, double* val) {
+  // basis vector -> up to two (flat index, coefficient) terms
+  int n, m;
+  if (plus) {
+    n = (int)floor((sqrt(8.0 * a + 1.0) - 1.0) * 0.5);
+    while ((n + 1) * (n + 2) / 2 <= a) ++n;
+    while (n * (n + 1) / 2 > a) --n;
+    m = a - n * (n + 1) / 2;
+  } else {
+    n = 1;
+    while (n * (n + 1) / 2 <= a) ++n;
+    m = a - n * (n - 1) / 2 + 1;
+  }
+  if (m == 0) {
+    idx[0] = n * n + n;
+    val[0] = 1.0;
+    return 1;
+  }
+  const double r = 0.70710678118654752440;
+  double s = (m & 1) ? -1.0 : 1.0;
+  idx[0] = n * n + n + m;
+  val[0] = r;
+  idx[1] = n * n + n - m;
+  val[1] = plus ? s * r : -s * r;
+  return 2;
+}
+
+__global__ void k_reac_split(int p, const cplx* __restrict__ full, cplx* __restrict__ out) {
+  const int P = (p + 1) * (p + 1);
+  const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long total = (long)np * np + (long)nm * nm;
+  if (e >= total) return;
+  bool plus = e < (long)np * np;
+  int nb = plus ? np : nm;
+  long le = plus ? e : e - (long)np * np;
+  int b = le / nb, a = le % nb;       // out[b][a] = v_a^T I v_b
+  int ia[2], ib[2];
+  double va[2], vb[2];
+  int na = basis_terms(p, a, plus, ia, va), nbt = basis_terms(p, b, plus, ib, vb);
+  cplx acc = C(0, 0);
+  for (int x = 0; x < na; ++x)
+    for (int y = 0; y < nbt; ++y)
+      acc = cadd(acc, cscale(full[(long)ib[y] * P + ia[x]], va[x] * vb[y]));    // I[i][j] at full[j*P + i]
+  out[e] = acc;
+}
+
 // ---------------------------------------------------------------- P2M
 
 
@@ -364,18 +418,19 @@ __device__ inline void regular_values(int p, double k, double dx, double dy, dou
   }
 }
 
-#define P2M_CHUNK 16
-__global__ void k_p2m(int p, const int* __restrict__ leaves, BoxGeom B, const CompGeom* __restrict__ cgs,
+// One CTA per source leaf: threads form the values of up to `chunk` sources
+// at a time in shared memory, then each thread sums its coefficients.
+__global__ void k_p2m(int p, int chunk, const int* __restrict__ leaves, BoxGeom B, const CompGeom* __restrict__ cgs,
                       const double* __restrict__ spos, const cplx* __restrict__ sq, cplx* __restrict__ M) {
   int b = leaves[blockIdx.x];
   const int P = (p + 1) * (p + 1);
   const CompGeom cg = cgs[B.comp[b]];
   double c[3];
   box_center(cg, B.lev[b], B.coord + 3 * b, c);
-  extern __shared__ cplx vals[];     // [P2M_CHUNK][P]
+  extern __shared__ cplx vals[];     // [chunk][P]
   cplx acc[4] = {C(0, 0), C(0, 0), C(0, 0), C(0, 0)};
-  for (int s0 = B.sb[b]; s0 < B.se[b]; s0 += P2M_CHUNK) {
-    int ns = min(P2M_CHUNK, B.se[b] - s0);
+  for (int s0 = B.sb[b]; s0 < B.se[b]; s0 += chunk) {
+    int ns = min(chunk, B.se[b] - s0);
     __syncthreads();
     for (int t = threadIdx.x; t < ns; t += blockDim.x) {
       int s = s0 + t;
@@ -435,98 +490,6 @@ __global__ void k_m2m(int p, const int* __restrict__ boxes, BoxGeom B, const lon
 // L_T = OpL2L[comp][level(T)][octant(T)] L_parent (if the parent carries a local
 // expansion) + sum_{S in V(T)} OpM2L(T, S) M_S.
 
-
-__global__ void k_m2l(int p, const int* __restrict__ boxes, int with_l2l, BoxGeom B, OpIndex OI,
-                      const int* __restrict__ voff, const int* __restrict__ vidx,
-                      const cplx* __restrict__ free_ops, const cplx* __restrict__ l2l_ops,
-                      const cplx* __restrict__ reac_ops, const cplx* __restrict__ M, cplx* __restrict__ L,
-                      int* __restrict__ err) {
-  int T = boxes[blockIdx.x];
-  const int P = (p + 1) * (p + 1);
-  extern __shared__ cplx xs[];
-  cplx acc[4] = {C(0, 0), C(0, 0), C(0, 0), C(0, 0)};
-  int mi[4];
-  for (int kk = 0; kk < 4; ++kk) {
-    int i = threadIdx.x + kk * blockDim.x;
-    int n = (int)floor(sqrt((double)i));
-    mi[kk] = i - n * n - n;
-  }
-  int comp = B.comp[T], lev = B.lev[T];
-  const CompGeom cg = OI.cgs[comp];
-  if (with_l2l) {
-    int pa = B.parent[T];
-    for (int i = threadIdx.x; i < P; i += blockDim.x) xs[i] = L[(long)pa * P + i];
-    __syncthreads();
-    int oct = (B.coord[3 * T] & 1) | ((B.coord[3 * T + 1] & 1) << 1) | ((B.coord[3 * T + 2] & 1) << 2);
-    const cplx* op = l2l_ops + OI.l2l_base[comp * 23 + lev] + (long)oct * P * P;
-    for (int kk = 0; kk < 4; ++kk) {
-      int i = threadIdx.x + kk * blockDim.x;
-      if (i >= P) break;
-      cplx a = acc[kk];
-      for (int j = 0; j < P; ++j) cfma(a, op[(long)j * P + i], xs[j]);
-      acc[kk] = a;
-    }
-  }
-  const int* ct = B.coord + 3 * T;
-  for (int e = voff[T]; e < voff[T + 1]; ++e) {
-    int S = vidx[e];
-    const int* cs = B.coord + 3 * S;
-    int dx = ct[0] - cs[0], dy = ct[1] - cs[1], dz = ct[2] - cs[2];
-    const cplx* op;
-    double phi = 0.0;
-    bool reac = cg.kind == CK_REAC;
-    if (!reac) {
-      long slot = ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
-      op = free_ops + OI.m2l_base[comp * 23 + lev] + slot * P * P;
-    } else {
-      int half = 1 << (lev - 1);
-      int jt, js;
-      if (cg.a == AR_UP) { jt = ct[2] - half; js = half - 1 - cs[2]; }
-      else { jt = half - 1 - ct[2]; js = cs[2] - half; }
-      int r2 = dx * dx + dy * dy, r = -1;
-      const int tab[10] = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18};
-      for (int k = 0; k < 10; ++k) if (tab[k] == r2) r = k;
-      long off = -1;
-      if (jt >= 0 && jt <= 1 && js >= 0 && js <= 1 && r >= 0)
-        off = OI.reac_off[((long)comp * 23 + lev) * 40 + (jt * 2 + js) * 10 + r];
-      if (off < 0) {
-        if (threadIdx.x == 0) atomicOr(err, 8);
-        continue;
-      }
-      op = reac_ops + off;
-      phi = atan2((double)dy, (double)dx);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
-      cplx v = M[(long)S * P + j];
-      if (reac) {
-        int n = (int)floor(sqrt((double)j)), m = j - n * n - n;
-        double sn, cn;
-        sincos(m * phi, &sn, &cn);
-        v = cmul(v, C(cn, sn));
-      }
-      xs[j] = v;
-    }
-    __syncthreads();
-    for (int kk = 0; kk < 4; ++kk) {
-      int i = threadIdx.x + kk * blockDim.x;
-      if (i >= P) break;
-      cplx a = C(0, 0);
-      for (int j = 0; j < P; ++j) cfma(a, op[(long)j * P + i], xs[j]);
-      if (reac) {
-        double sn, cn;
-        sincos(mi[kk] * phi, &sn, &cn);
-        a = cmul(a, C(cn, -sn));
-      }
-      acc[kk] = cadd(acc[kk], a);
-    }
-  }
-  for (int kk = 0; kk < 4; ++kk) {
-    int i = threadIdx.x + kk * blockDim.x;
-    if (i >= P) break;
-    L[(long)T * P + i] = acc[kk];
-  }
-}
 
 // Mark the reaction M2L classes used by the V lists:
 // used[(comp * 23 + level) * 40 + (jt * 2 + js) * 10 + r] = 1.
@@ -633,15 +596,16 @@ void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const d
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
                 const cplx* sq, cplx* M, cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  size_t smem = sizeof(cplx) * P2M_CHUNK * P;
+  int chunk = std::min(16, (int)((200 * 1024) / (sizeof(cplx) * P)));
+  size_t smem = sizeof(cplx) * chunk * P;
   cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (n) LAUNCH(k_p2m<<<n, 128, smem, st>>>(p, leaves, B, cgs, spos, sq, M));
+  if (n) LAUNCH(k_p2m<<<n, 128, smem, st>>>(p, chunk, leaves, B, cgs, spos, sq, M));
 }
 
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
                 const cplx* L, cplx* phi, cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  if (n) LAUNCH(k_l2p<<<n, 128, sizeof(cplx) * P, st>>>(p, leaves, B, cgs, tpos, L, phi));
+  if (n) LAUNCH(k_l2p<<<n, 64, sizeof(cplx) * P, st>>>(p, leaves, B, cgs, tpos, L, phi));
 }
 
 void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, const cplx* ops, cplx* M,
@@ -650,12 +614,10 @@ void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, 
   if (n) LAUNCH(k_m2m<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, B, op_base, ops, M));
 }
 
-void launch_m2l(int p, const int* boxes, int n, int with_l2l, BoxGeom B, OpIndex OI, const int* voff,
-                const int* vidx, const cplx* free_ops, const cplx* l2l_ops, const cplx* reac_ops, const cplx* M,
-                cplx* L, int* err, cudaStream_t st) {
-  int P = (p + 1) * (p + 1);
-  if (n) LAUNCH(k_m2l<<<n, 128, sizeof(cplx) * P, st>>>(p, boxes, with_l2l, B, OI, voff, vidx, free_ops, l2l_ops,
-                                                        reac_ops, M, L, err));
+void launch_reac_split(int p, const cplx* full, cplx* out, cudaStream_t st) {
+  long np = (long)(p + 1) * (p + 2) / 2, nm = (long)p * (p + 1) / 2;
+  long total = np * np + nm * nm;
+  LAUNCH(k_reac_split<<<(total + 255) / 256, 256, 0, st>>>(p, full, out));
 }
 
 void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,

@@ -58,6 +58,9 @@ __device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coe
 
 
 #define NEAR_CHUNK 128
+// One CTA (128 threads) per target leaf: thread pairs (t, t + 64) share a
+// target and take alternate sources; the two halves are added at the end in
+// a fixed order.
 __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearComp* __restrict__ ncs,
                        RuleView R, const double* __restrict__ spos, const cplx* __restrict__ sq,
                        const double* __restrict__ tpos, cplx* __restrict__ phi,
@@ -67,11 +70,15 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
   const NearComp nc = ncs[B.comp[T]];
   __shared__ double sx[NEAR_CHUNK], sy[NEAR_CHUNK], sz[NEAR_CHUNK];
   __shared__ cplx sqs[NEAR_CHUNK];
+  __shared__ cplx half1[64];
   const cplx* coef = R.coef + nc.coef_off;
   const cplx* kzl = R.kz + (long)nc.l * R.Q;
   const cplx* kzp = R.kz + (long)nc.lp * R.Q;
-  for (int t0 = B.tb[T]; t0 < B.te[T]; t0 += blockDim.x) {
-    int t = t0 + threadIdx.x;
+  const int lane_t = threadIdx.x & 63, par = threadIdx.x >> 6;
+  const double k = nc.k;
+  const double inv4pi = 1.0 / (4.0 * FMM_PI);
+  for (int t0 = B.tb[T]; t0 < B.te[T]; t0 += 64) {
+    int t = t0 + lane_t;
     bool act = t < B.te[T];
     double x = 0, y = 0, z = 0;
     if (act) { x = tpos[3 * t]; y = tpos[3 * t + 1]; z = tpos[3 * t + 2]; }
@@ -96,31 +103,33 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
       for (int s0 = B.sb[S]; s0 < B.se[S]; s0 += NEAR_CHUNK) {
         int ns = min(NEAR_CHUNK, B.se[S] - s0);
         __syncthreads();
-        for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-          sx[k] = spos[3 * (s0 + k)]; sy[k] = spos[3 * (s0 + k) + 1]; sz[k] = spos[3 * (s0 + k) + 2];
-          sqs[k] = sq[s0 + k];
+        for (int kk = threadIdx.x; kk < ns; kk += blockDim.x) {
+          sx[kk] = spos[3 * (s0 + kk)]; sy[kk] = spos[3 * (s0 + kk) + 1]; sz[kk] = spos[3 * (s0 + kk) + 2];
+          sqs[kk] = sq[s0 + kk];
         }
         __syncthreads();
         if (act) {
           if (nc.kind == CK_FREE) {
-            for (int k = 0; k < ns; ++k) {
-              double dx = x - sx[k], dy = y - sy[k], dz = z - sz[k];
-              if (dx == 0.0 && dy == 0.0 && dz == 0.0) continue;
-              double r = sqrt(dx * dx + dy * dy + dz * dz);
-              double s, c;
-              sincos(nc.k * r, &s, &c);
-              double f = 1.0 / (4.0 * FMM_PI * r);
-              cfma(acc, C(c * f, s * f), sqs[k]);
+            for (int kk = par; kk < ns; kk += 2) {
+              double dx = x - sx[kk], dy = y - sy[kk], dz = z - sz[kk];
+              if (dx == 0.0 && dy == 0.0 && dz == 0.0) continue;   // bitwise-identical points (j = i)
+              double r2 = dx * dx + dy * dy + dz * dz;
+              double rinv = rsqrt(r2);
+              double r = r2 * rinv;
+              double sn, cs;
+              sincos(k * r, &sn, &cs);
+              double f = rinv * inv4pi;
+              cfma(acc, C(cs * f, sn * f), sqs[kk]);
               ++my_pairs;
             }
           } else {
             double zt = fabs(z - nc.dref);
-            for (int k = 0; k < ns; ++k) {
-              double dx = x - sx[k], dy = y - sy[k];
+            for (int kk = par; kk < ns; kk += 2) {
+              double dx = x - sx[kk], dy = y - sy[kk];
               double rho = sqrt(dx * dx + dy * dy);
-              double zs = fabs(sz[k] - nc.dref);
+              double zs = fabs(sz[kk] - nc.dref);
               int nq;
-              cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs, &nq), sqs[k]);
+              cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs, &nq), sqs[kk]);
               ++my_pairs;
               my_nodes += nq;
             }
@@ -128,7 +137,10 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
         }
       }
     }
-    if (act) phi[t] = cadd(phi[t], acc);
+    __syncthreads();
+    if (par == 1) half1[lane_t] = acc;
+    __syncthreads();
+    if (par == 0 && act) phi[t] = cadd(phi[t], cadd(acc, half1[lane_t]));
   }
   if (counters && my_pairs) {
     atomicAdd(&counters[0], my_pairs);
@@ -259,7 +271,7 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
                  const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st) {
-  if (n) LAUNCH(k_near<<<n, 64, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
+  if (n) LAUNCH(k_near<<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
 }
 
 // Dependent FP64 FMA chains (8 independent chains per thread).
