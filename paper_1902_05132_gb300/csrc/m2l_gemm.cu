@@ -125,6 +125,9 @@ __global__ void k_m2l_gather(long nv, int p, const int* __restrict__ perm, const
 struct GemmBatch {
   long a_off, y_off, z_off;
   int R, C, K, ldy, ldz;
+  int r0, RB;            // rows r0 .. r0 + RB of the operator handled by this batch
+  int CB;                // contraction chunk staged in shared memory (C: operator resident)
+  int TK;                // thread columns; the input tile is TK * Z_KB columns of CB entries
 };
 // One CTA per batch: the operator (R x C, input-major) stays in shared
 // memory; columns stream through in tiles of TK*KB.  Thread (tr, tk) owns rows
@@ -134,55 +137,65 @@ struct GemmBatch {
 __global__ void __launch_bounds__(128) k_zgemm_res(const GemmBatch* __restrict__ batches, const cplx* __restrict__ A,
                                                    const cplx* __restrict__ Y, cplx* __restrict__ Z) {
   const GemmBatch bt = batches[blockIdx.x];
-  const int R = bt.R, Cc = bt.C, K = bt.K;
+  const int R = bt.RB, Cc = bt.C, K = bt.K, CB = bt.CB;   // R: rows of this block, CB: contraction chunk
   const int TR = (R + Z_RPT - 1) / Z_RPT;
-  const int TK = 128 / TR;
+  const int TK = bt.TK;                                    // TR * TK <= 128, chosen by the host
   const int KT = TK * Z_KB;
   extern __shared__ cplx sm[];
-  cplx* As = sm;                      // [C][R]
-  cplx* Ys = As + (size_t)R * Cc;     // [KT][C]
+  cplx* As = sm;                      // [CB][RB]
+  cplx* Ys = As + (size_t)R * CB;     // [KT][CB]
   const cplx* Ab = A + bt.a_off;
-  for (int e = threadIdx.x; e < R * Cc; e += blockDim.x) As[e] = Ab[e];
   const int tr = threadIdx.x % TR, tk = threadIdx.x / TR;
   const bool act = tk < TK;
   const cplx* Yb = Y + bt.y_off;
   cplx* Zb = Z + bt.z_off;
+  int rows[Z_RPT];
+#pragma unroll
+  for (int i = 0; i < Z_RPT; ++i) rows[i] = min(tr + TR * i, R - 1);
   for (int k0 = 0; k0 < K; k0 += KT) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < KT * Cc; e += blockDim.x) {
-      int kk = e / Cc, c = e % Cc;
-      int k = k0 + kk;
-      Ys[e] = (k < K) ? Yb[(long)k * bt.ldy + c] : C(0, 0);
-    }
-    __syncthreads();
-    if (!act) continue;
     cplx acc[Z_RPT][Z_KB];
 #pragma unroll
     for (int i = 0; i < Z_RPT; ++i)
 #pragma unroll
       for (int j = 0; j < Z_KB; ++j) acc[i][j] = C(0, 0);
-    int rows[Z_RPT];
-#pragma unroll
-    for (int i = 0; i < Z_RPT; ++i) rows[i] = min(tr + TR * i, R - 1);
+    for (int c0 = 0; c0 < Cc; c0 += CB) {
+      const int cb = min(CB, Cc - c0);
+      __syncthreads();
+      if (k0 == 0 || CB < Cc)         // a resident operator is staged once
+        for (int e = threadIdx.x; e < R * cb; e += blockDim.x) {
+          int c = e / R, rr = e % R;
+          As[e] = Ab[(long)(c0 + c) * bt.R + bt.r0 + rr];
+        }
+      for (int e = threadIdx.x; e < KT * cb; e += blockDim.x) {
+        int kk = e / cb, c = e % cb;
+        int k = k0 + kk;
+        Ys[e] = (k < K) ? Yb[(long)k * bt.ldy + c0 + c] : C(0, 0);
+      }
+      __syncthreads();
+      if (act) {
 #pragma unroll 2
-    for (int c = 0; c < Cc; ++c) {
-      cplx a[Z_RPT], y[Z_KB];
+        for (int c = 0; c < cb; ++c) {
+          cplx a[Z_RPT], y[Z_KB];
 #pragma unroll
-      for (int i = 0; i < Z_RPT; ++i) a[i] = As[c * R + rows[i]];
+          for (int i = 0; i < Z_RPT; ++i) a[i] = As[c * R + rows[i]];
 #pragma unroll
-      for (int j = 0; j < Z_KB; ++j) y[j] = Ys[(tk + TK * j) * Cc + c];
+          for (int j = 0; j < Z_KB; ++j) y[j] = Ys[(tk + TK * j) * cb + c];
+#pragma unroll
+          for (int i = 0; i < Z_RPT; ++i)
+#pragma unroll
+            for (int j = 0; j < Z_KB; ++j) cfma(acc[i][j], a[i], y[j]);
+        }
+      }
+    }
+    if (act) {
 #pragma unroll
       for (int i = 0; i < Z_RPT; ++i)
 #pragma unroll
-        for (int j = 0; j < Z_KB; ++j) cfma(acc[i][j], a[i], y[j]);
+        for (int j = 0; j < Z_KB; ++j) {
+          int r = tr + TR * i, k = k0 + tk + TK * j;
+          if (r < R && k < K) Zb[(long)k * bt.ldz + bt.r0 + r] = acc[i][j];
+        }
     }
-#pragma unroll
-    for (int i = 0; i < Z_RPT; ++i)
-#pragma unroll
-      for (int j = 0; j < Z_KB; ++j) {
-        int r = tr + TR * i, k = k0 + tk + TK * j;
-        if (r < R && k < K) Zb[(long)k * bt.ldz + r] = acc[i][j];
-      }
   }
 }
 
@@ -248,6 +261,48 @@ __global__ void k_inverse_perm(long n, const int* __restrict__ perm, int* __rest
   if (k < n) inv[perm[k]] = (int)k;
 }
 
+// Shared memory of a CTA holding RB operator rows of a CB-wide contraction
+// chunk plus TK * Z_KB input columns of that chunk.
+static size_t gemm_smem(int RB, int CB, int TK) {
+  return sizeof(cplx) * ((size_t)RB * CB + (size_t)TK * Z_KB * CB);
+}
+static const size_t kGemmSmemCap = 200 * 1024;
+// Thread columns of a block of RB rows: as many as 128 threads allow, fewer
+// if the input tile would not fit beside the operator block.
+static int gemm_tk(int RB, int CB) {
+  int TK = 128 / ((RB + Z_RPT - 1) / Z_RPT);
+  while (TK > 1 && gemm_smem(RB, CB, TK) > kGemmSmemCap) --TK;
+  return TK;
+}
+// Tile of an R x R operator: the whole operator resident if it fits, else
+// row blocks of it (each resident), else 96-row blocks streamed in chunks
+// of the contraction.  Every block, the ragged last one included, fits.
+static void gemm_tiles(int R, int& RB, int& CB) {
+  auto full_tk = [](int rb) { return 128 / ((rb + Z_RPT - 1) / Z_RPT); };
+  RB = std::min(R, 3 * 128);
+  CB = R;
+  while (RB > 3 && gemm_smem(RB, CB, full_tk(RB)) > kGemmSmemCap) RB -= 3;
+  if (gemm_smem(RB, CB, full_tk(RB)) <= kGemmSmemCap) return;
+  RB = std::min(R, 96);
+  CB = (int)(kGemmSmemCap / gemm_smem(RB, 1, full_tk(RB)));
+}
+static int R_blocks(int R) {
+  int RB, CB;
+  gemm_tiles(R, RB, CB);
+  return (R + RB - 1) / RB;
+}
+// Largest shared memory of any block of an R x R operator.
+static size_t gemm_smem_max(int R) {
+  int RB, CB;
+  gemm_tiles(R, RB, CB);
+  size_t m = 0;
+  for (int r0 = 0; r0 < R; r0 += RB) {
+    int rb = std::min(RB, R - r0);
+    m = std::max(m, gemm_smem(rb, CB, gemm_tk(rb, CB)));
+  }
+  return m;
+}
+
 // Host driver: all V pairs of all levels.  L receives the M2L part for every
 // box with targets at level >= 2; then L2L level by level.
 void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
@@ -307,12 +362,16 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
       // one batch per operator block, split into chunks of at most 128
       // columns so that large classes spread over several CTAs
       auto add = [&](long a_off, int R, long yz) {
-        for (int c0 = 0; c0 < K; c0 += 128) {
-          GemmBatch g{};
-          g.a_off = a_off; g.R = R; g.C = R; g.K = std::min(128, K - c0);
-          g.y_off = (k0 + c0) * P + yz; g.z_off = (k0 + c0) * P + yz; g.ldy = P; g.ldz = P;
-          bat.push_back(g);
-        }
+        int RB, CB;
+        gemm_tiles(R, RB, CB);
+        for (int r0 = 0; r0 < R; r0 += RB)
+          for (int c0 = 0; c0 < K; c0 += 128) {
+            GemmBatch g{};
+            g.a_off = a_off; g.R = R; g.C = R; g.K = std::min(128, K - c0);
+            g.y_off = (k0 + c0) * P + yz; g.z_off = (k0 + c0) * P + yz; g.ldy = P; g.ldz = P;
+            g.r0 = r0; g.RB = std::min(RB, R - r0); g.CB = CB; g.TK = gemm_tk(g.RB, CB);
+            bat.push_back(g);
+          }
       };
       if (!reac) {
         add(off, P, 0);
@@ -332,17 +391,14 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
       for (int r = 0; r < nruns; ++r) {
         bool reac = hk[r] & 1;
         int nchunk = (hc[r] + 127) / 128;
-        int nblk = (reac && nm) ? 2 : 1;
-        for (int c = 0; c < nchunk * nblk; ++c) (reac ? breac : bfree).push_back(bat[bi++]);
+        int nb_rows = reac ? (R_blocks(np) + (nm ? R_blocks(nm) : 0)) : R_blocks(P);
+        for (int c = 0; c < nchunk * nb_rows; ++c) (reac ? breac : bfree).push_back(bat[bi++]);
       }
     }
     std::vector<GemmBatch> ordered = bfree;
     ordered.insert(ordered.end(), breac.begin(), breac.end());
     FMM_CHECK(cudaMemcpyAsync(dbat, ordered.data(), sizeof(GemmBatch) * ordered.size(), cudaMemcpyHostToDevice, st));
-    auto smem_of = [&](int R) {
-      int TR = (R + 2) / 3, TK = 128 / TR, KT = TK * 4;
-      return sizeof(cplx) * ((size_t)R * R + (size_t)KT * R);
-    };
+    auto smem_of = [&](int R) { return gemm_smem_max(R); };
     size_t smax = std::max(smem_of(P), std::max(smem_of(np), nm ? smem_of(nm) : (size_t)0));
     cudaFuncSetAttribute(k_zgemm_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     if (!bfree.empty())

@@ -247,17 +247,20 @@ __global__ void k_reac_contract(int p, int Q, int n_near, const cplx* __restrict
   const int D = 2 * p + 1;
   const int am = abs(m), nrow = p + 1 - am;
   const int nout = nrow * P;
+  // outputs of this CTA: obase .. obase + 8 * blockDim.x (blockIdx.z splits large orders)
+  const int obase = blockIdx.z * 8 * blockDim.x;
+  if (obase >= nout) return;        // uniform over the CTA
   extern __shared__ double smr[];
   // tail tiles: A[TQR][nrow], B[TQR][P], J[TQR][D]; near tiles reuse the space as complex
   double* sA = smr;
   double* sB = sA + 2 * TQR * (FMM_MAXP + 1);
   double* sJ = sB + 2 * TQR * P;
-  const int per = (nout + blockDim.x - 1) / blockDim.x;
+  const int per = (nout - obase + blockDim.x - 1) / blockDim.x;
   double accr[8], acci[8];
   int oi[8], oj[8], od[8];
   for (int k = 0; k < 8; ++k) {
     accr[k] = acci[k] = 0.0;
-    int o = threadIdx.x + k * blockDim.x;
+    int o = obase + threadIdx.x + k * blockDim.x;
     oi[k] = o / P;
     oj[k] = o % P;
     int n2 = (int)floor(sqrt((double)oj[k])), mm = oj[k] - n2 * n2 - n2;
@@ -279,7 +282,7 @@ __global__ void k_reac_contract(int p, int Q, int n_near, const cplx* __restrict
     for (int e = threadIdx.x; e < nq * D; e += blockDim.x) cJ[e] = Jc[((long)r * n_near + q0) * D + e];
     __syncthreads();
     for (int k = 0; k < per && k < 8; ++k) {
-      int o = threadIdx.x + k * blockDim.x;
+      int o = obase + threadIdx.x + k * blockDim.x;
       if (o >= nout) break;
       int d = od[k], ad = abs(d);
       double sgnd = (d < 0 && (ad & 1)) ? -1.0 : 1.0;
@@ -312,7 +315,7 @@ __global__ void k_reac_contract(int p, int Q, int n_near, const cplx* __restrict
     for (int e = threadIdx.x; e < nq * D; e += blockDim.x) sJ[e] = Jr[((long)r * Qt + q0) * D + e];
     __syncthreads();
     for (int k = 0; k < per && k < 8; ++k) {
-      int o = threadIdx.x + k * blockDim.x;
+      int o = obase + threadIdx.x + k * blockDim.x;
       if (o >= nout) break;
       int d = od[k], ad = abs(d);
       double sgnd = (d < 0 && (ad & 1)) ? -1.0 : 1.0;
@@ -322,7 +325,7 @@ __global__ void k_reac_contract(int p, int Q, int n_near, const cplx* __restrict
     }
   }
   for (int k = 0; k < per && k < 8; ++k) {
-    int o = threadIdx.x + k * blockDim.x;
+    int o = obase + threadIdx.x + k * blockDim.x;
     if (o >= nout) break;
     int n = am + oi[k];
     int i = n * n + n + m;
@@ -587,9 +590,8 @@ void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const d
   LAUNCH(k_reac_bessel<<<(ne + 127) / 128, 128, 0, st>>>(p, g.Q, nn, nr, d_rho, R.kr.as<cplx>(), Jc, Jr));
   size_t smem = sizeof(double) * (2 * TQR * (FMM_MAXP + 1) + 2 * TQR * P + 2 * TQR * D);
   cudaFuncSetAttribute(k_reac_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int threads = 256;
-  while ((p + 1) * P > 8 * threads && threads < 1024) threads *= 2;
-  dim3 grid(nr, 2 * p + 1);
+  const int threads = 256;
+  dim3 grid(nr, 2 * p + 1, ((p + 1) * P + 8 * threads - 1) / (8 * threads));
   LAUNCH(k_reac_contract<<<grid, threads, smem, st>>>(p, g.Q, nn, Ac, Bc, Ar, Br, Jc, Jr, d_out_off, ops));
 }
 
