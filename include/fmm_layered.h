@@ -123,6 +123,28 @@ int fmm_layered_eval(fmm_layered_t* h, long n_src, const double* src_xyz,
                      const double* charges, long n_tgt, const double* tgt_xyz,
                      double* out, void* stream);
 
+/*
+ * Batched evaluation of n independent problems (the components of different
+ * problems never interact, as the components of one problem are summed only
+ * at the end: eq. totalinteraction).  Problem i uses handle hs[i] (its own
+ * medium, p and leaf size) and the device buffers src_xyz[i], charges[i],
+ * tgt_xyz[i], out[i] laid out as in fmm_layered_eval, with n_src[i] sources
+ * and n_tgt[i] targets.  The handles must be distinct: a handle holds the
+ * workspace of one problem at a time.
+ * The problems run concurrently, each on a stream of its own handle that
+ * first waits for the work already queued on `stream` (the inputs); when
+ * the call returns, `stream` is ordered after every problem that succeeded.
+ * Results are identical to n separate fmm_layered_eval calls.
+ * Returns FMM_OK, FMM_ERR_ARG (bad arrays or a repeated handle, nothing
+ * run), or the code of the first failed problem (in index order); the
+ * message of each failed problem is fmm_layered_last_error(hs[i]), and the
+ * outputs of the problems that did not fail are valid.
+ */
+int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const long* n_src,
+                             const double* const* src_xyz, const double* const* charges,
+                             const long* n_tgt, const double* const* tgt_xyz,
+                             double* const* out, void* stream);
+
 /* Same as fmm_layered_eval with HOST buffers: copies inputs to the device,
  * evaluates and copies the potentials back (all on `stream`). */
 int fmm_layered_eval_host(fmm_layered_t* h, long n_src, const double* src_xyz,

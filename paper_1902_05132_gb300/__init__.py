@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
             "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
             "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
-            "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc"]
+            "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched"]
 
 _lib = None
 
@@ -73,6 +73,8 @@ def lib():
         f = getattr(L, name)
         f.argtypes = [v, l, d, d, l, d, d, v]
         f.restype = i
+    L.fmm_layered_eval_batched.argtypes = [i, d, d, d, d, d, d, d, v]
+    L.fmm_layered_eval_batched.restype = i
     L.fmm_layered_stats.argtypes = [v, ctypes.POINTER(Stats)]
     L.fmm_layered_stats.restype = i
     L.fmm_layered_num_components.argtypes = [v]
@@ -85,6 +87,40 @@ def lib():
     L.fmm_layered_measure_fp64_peak.restype = i
     _lib = L
     return L
+
+
+def eval_batched(solvers, problems, outs=None, stream=None):
+    """Evaluate independent problems concurrently (fmm_layered_eval_batched).
+
+    solvers: distinct LayeredFMM handles; problems: (src, q, tgt) device
+    tensors per handle.  Returns the list of potentials."""
+    import torch
+    n = len(solvers)
+    if len(problems) != n or len({id(s) for s in solvers}) != n:
+        raise ValueError("one distinct solver per problem")
+    args = [LayeredFMM._dev_args(*pr) for pr in problems]
+    if outs is None:
+        outs = [torch.empty(t.shape[0], dtype=torch.complex128, device=t.device) for _, _, t in args]
+    outr = [torch.view_as_real(o) for o in outs]
+    P = ctypes.c_void_p * n
+    Lg = ctypes.c_long * n
+    hs = P(*[s.h for s in solvers])
+    ns = Lg(*[a[0].shape[0] for a in args])
+    nt = Lg(*[a[2].shape[0] for a in args])
+    src = P(*[_ptr(a[0]) for a in args])
+    q = P(*[_ptr(a[1]) for a in args])
+    tgt = P(*[_ptr(a[2]) for a in args])
+    out = P(*[_ptr(o) for o in outr])
+    if stream is None:
+        stream = torch.cuda.current_stream(args[0][2].device if n else None)
+    rc = lib().fmm_layered_eval_batched(n, ctypes.cast(hs, ctypes.c_void_p), ctypes.cast(ns, ctypes.c_void_p),
+                                        ctypes.cast(src, ctypes.c_void_p), ctypes.cast(q, ctypes.c_void_p),
+                                        ctypes.cast(nt, ctypes.c_void_p), ctypes.cast(tgt, ctypes.c_void_p),
+                                        ctypes.cast(out, ctypes.c_void_p), ctypes.c_void_p(stream.cuda_stream))
+    if rc != 0:
+        msgs = [lib().fmm_layered_last_error(s.h).decode() for s in solvers]
+        raise FmmError(rc, "; ".join(f"problem {i}: {m}" for i, m in enumerate(msgs) if m) or "invalid argument")
+    return outs
 
 
 def _ptr(a):

@@ -3,7 +3,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <set>
+#include <thread>
 #include <vector>
 
 #include "fmm_internal.h"
@@ -43,7 +46,7 @@ void tree_host_copy(fmm_layered* h, std::vector<int>& comp, std::vector<int>& le
                     std::vector<int>& tb, std::vector<int>& te, std::vector<int>& parent);
 
 static thread_local std::string g_create_err;
-long g_fmm_launches = 0;
+thread_local long g_fmm_launches = 0;
 
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t0) {
@@ -143,6 +146,8 @@ extern "C" int fmm_layered_create(int n_layers, const double* k, const double* i
 
 extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   if (!h) return;
+  if (h->bstream) cudaStreamDestroy(h->bstream);
+  if (h->bdone) cudaEventDestroy(h->bdone);
   DevBuf* all[] = {&h->d_k, &h->d_d, &h->d_eps, &h->rule.kr, &h->rule.w, &h->rule.kz, &h->rule.sigma,
                    &h->tab.gaunt, &h->tab.phase};
   for (DevBuf* b : all) b->release();
@@ -641,6 +646,73 @@ extern "C" int fmm_layered_eval(fmm_layered_t* h, long ns, const double* src, co
   return FMM_OK;
 }
 
+// Independent problems, each with its own handle, evaluated concurrently: one
+// host thread per problem (up to 16 at a time) drives that problem's
+// evaluation on the handle's own stream, so that the kernels of different
+// problems overlap on the GPU while each thread waits on its own host steps.
+extern "C" int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const long* ns, const double* const* src,
+                                        const double* const* q, const long* nt, const double* const* tgt,
+                                        double* const* out, void* stream) {
+  if (n < 0 || (n > 0 && (!hs || !ns || !src || !q || !nt || !tgt || !out))) return FMM_ERR_ARG;
+  std::set<const fmm_layered_t*> seen;
+  for (int i = 0; i < n; ++i) {
+    fmm_layered* h = hs[i];
+    if (!h || !seen.insert(h).second) return FMM_ERR_ARG;     // a handle serves one problem at a time
+    h->err.clear();
+    if (ns[i] < 0 || nt[i] < 0 || (ns[i] && (!src[i] || !q[i])) || (nt[i] && (!tgt[i] || !out[i]))) {
+      h->err = "invalid argument";
+      return FMM_ERR_ARG;
+    }
+  }
+  if (n == 0) return FMM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ready = nullptr;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return FMM_ERR_CUDA;
+  if (cudaEventRecord(ready, st) != cudaSuccess) {
+    cudaEventDestroy(ready);
+    return FMM_ERR_CUDA;
+  }
+  std::vector<int> rc(n, FMM_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      int i = next.fetch_add(1);
+      if (i >= n) break;
+      fmm_layered* h = hs[i];
+      try {
+        FMM_CHECK(cudaSetDevice(h->dev));
+        if (!h->bstream) FMM_CHECK(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking));
+        if (!h->bdone) FMM_CHECK(cudaEventCreateWithFlags(&h->bdone, cudaEventDisableTiming));
+        FMM_CHECK(cudaStreamWaitEvent(h->bstream, ready, 0));      // inputs written on the caller's stream
+        eval_impl(h, ns[i], src[i], q[i], nt[i], tgt[i], out[i], h->bstream);
+        FMM_CHECK(cudaEventRecord(h->bdone, h->bstream));
+        h->nsrc_last = ns[i];
+        h->ntgt_last = nt[i];
+      } catch (FmmError& e) {
+        h->err = e.msg;
+        rc[i] = e.code;
+      } catch (std::exception& e) {
+        h->err = e.what();
+        rc[i] = FMM_ERR_OOM;
+      }
+    }
+  };
+  int nth = std::min(n, 16);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  int first = FMM_OK;
+  for (int i = 0; i < n; ++i) {
+    if (rc[i] == FMM_OK) {
+      if (cudaStreamWaitEvent(st, hs[i]->bdone, 0) != cudaSuccess && first == FMM_OK) first = FMM_ERR_CUDA;
+    } else if (first == FMM_OK) {
+      first = rc[i];
+    }
+  }
+  cudaEventDestroy(ready);
+  return first;
+}
+
 extern "C" int fmm_layered_eval_host(fmm_layered_t* h, long ns, const double* src, const double* q, long nt,
                                      const double* tgt, double* out, void* stream) {
   if (!h) return FMM_ERR_ARG;
@@ -709,6 +781,8 @@ extern "C" int fmm_layered_tree_export(const fmm_layered_t* hc, int c, int* leve
   fmm_layered* h = const_cast<fmm_layered*>(hc);
   if (!h || c < 0 || c >= (int)h->comps.size()) return FMM_ERR_ARG;
   const Comp& C_ = h->comps[c];
+  // the evaluation may have run on any stream: let it finish before reading its trees
+  if (cudaDeviceSynchronize() != cudaSuccess) return FMM_ERR_CUDA;
   std::vector<int> comp, lev, sb, se, tb, te, par;
   std::vector<unsigned long long> pre;
   tree_host_copy(h, comp, lev, pre, sb, se, tb, te, par);

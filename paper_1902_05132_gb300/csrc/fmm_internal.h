@@ -153,10 +153,15 @@ struct fmm_layered {
   std::vector<int> lvl_begin;         // global box index where each level starts
   int nboxes = 0;
   long nsrc_last = 0, ntgt_last = 0;
+  // stream and completion event of this handle's problem in a batched call
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t bdone = nullptr;
 };
 
-// Count of this library's kernel launches (CUB's internal launches excluded).
-extern long g_fmm_launches;
+// Count of this library's kernel launches made by the calling host thread
+// (CUB's internal launches excluded).  Per thread, so that the problems of a
+// batched call, each evaluated by its own host thread, count their own.
+extern thread_local long g_fmm_launches;
 #define LAUNCH(...) do { ++g_fmm_launches; __VA_ARGS__; } while (0)
 
 // ---- plain-data structures passed to kernels

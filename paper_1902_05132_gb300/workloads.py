@@ -63,3 +63,35 @@ def sample_targets(n, count, seed=1):
     rng = np.random.default_rng(seed)
     count = min(count, n)
     return np.sort(rng.choice(n, size=count, replace=False))
+
+
+def batched(n_problems=64, seed=0, n_min=10_000, n_max=200_000, p=10, leaf=64):
+    """Independent problems of uneven size: N log-uniform in [n_min, n_max],
+    2-5 layers, interior layer thickness U[0.8, 1.5] (first interface at
+    z = 0), k_l ~ U[0.5, 3.0], eps_l = 1 + l, real charges U[0,1], targets =
+    sources.  Points lie in [-1,1]^2 x slabs kept 0.1 away from the
+    interfaces: the interior of each interior layer, and a slab of thickness
+    1 on the far side of the top and bottom interfaces; a layer receives
+    points in proportion to its slab thickness."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_problems):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        L1 = int(rng.integers(2, 6))
+        d = [0.0]
+        for _ in range(L1 - 2):
+            d.append(d[-1] - rng.uniform(0.8, 1.5))
+        k = list(rng.uniform(0.5, 3.0, L1))
+        eps = [1.0 + l for l in range(L1)]
+        slabs = [(d[0] + 0.1, d[0] + 1.1)]
+        for j in range(1, L1 - 1):
+            slabs.append((d[j] + 0.1, d[j - 1] - 0.1))
+        slabs.append((d[-1] - 1.1, d[-1] - 0.1))
+        th = np.array([hi - lo for lo, hi in slabs])
+        counts = np.floor(n * th / th.sum()).astype(int)
+        counts[: n - counts.sum()] += 1
+        src = np.concatenate([_cube(rng, m, lo, hi) for m, (lo, hi) in zip(counts, slabs)])
+        q = rng.uniform(0.0, 1.0, n).astype(complex)
+        out.append(dict(k=k, d=d, eps=eps, p=p, leaf=leaf, src=src, q=q, tgt=src.copy(),
+                        name=f"batched problem {i}: N={n}, {L1} layers"))
+    return out
