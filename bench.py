@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -32,6 +33,10 @@ if ROOT not in sys.path:
 WORKLOAD = dict(name="three-layer N=32768 p=8 leaf=64", n=32768, p=8, leaf=64)
 METRIC = "FMM particles/sec at rel L2 err 1e-6 (FP64)"
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) of the M2L product launches of one evaluation of
+# the workload, from an ncu capture of the current kernel (None once the
+# kernel changes); the capture command is in the profile summary of the kernel.
+NCU_TRAFFIC = {}
 
 
 def _dist():
@@ -74,22 +79,6 @@ def _clock_summary(path):
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
             "samples": len(sm)}
-
-
-def _algorithmic(stats, p, n):
-    """Algorithmic FP64 flops of each stage (conventions stated in the design doc)."""
-    P2 = (p + 1) ** 2
-    P4 = P2 * P2
-    # reaction M2L: the radial operator splits into blocks of (p+1)(p+2)/2 and
-    # p(p+1)/2 rows (m-reflection symmetry), one complex MAC per block entry
-    split = ((p + 1) * (p + 2) // 2) ** 2 + (p * (p + 1) // 2) ** 2
-    n_free_v = stats["n_v_pairs"] - stats["n_v_pairs_reac"]
-    return {
-        "near_reac": 60.0 * stats["n_reac_nodes"],
-        "near_free": 30.0 * stats["n_free_pairs"],
-        "m2l": 8.0 * (P4 * n_free_v + split * stats["n_v_pairs_reac"]),
-        "operators": 8.0 * P4 * stats["n_reac_T_nodes"],
-    }
 
 
 def cpu_oracle_sample(n_targets, seed=0):
@@ -173,8 +162,9 @@ def main():
     for _ in range(max(3, args.warmup)):
         solver.eval(src, q, tgt, out=out)
     torch.cuda.synchronize()
-    clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
-    os.makedirs(os.path.dirname(clock_path), exist_ok=True)
+    clock_dir = os.environ.get("FMM_BENCH_CLOCKS_DIR") or tempfile.mkdtemp(prefix="fmm_bench_")
+    os.makedirs(clock_dir, exist_ok=True)
+    clock_path = os.path.join(clock_dir, f"bench_clocks_r{rank}.csv")
     sampler = _clock_sampler(clock_path, local)
     time.sleep(0.3)
     if ws > 1:
@@ -182,6 +172,7 @@ def main():
     torch.cuda.synchronize()
     ms, stage = [], []
     launches = 0
+    torch.cuda.nvtx.range_push("timed")      # lets a profiler select the timed steps
     for _ in range(args.steps):
         flush.fill_(1.0)                      # evict the L2 between steps
         torch.cuda.synchronize()
@@ -194,6 +185,7 @@ def main():
         st = solver.stats()
         stage.append(st)
         launches += st["n_launches"]
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -242,10 +234,13 @@ def main():
     # roofline of the dominant stage (FP64 pipe, peak measured on this GPU now)
     keys = ["tree", "operators", "upward", "m2l", "l2p", "near_free", "near_reac", "sum"]
     mean_stage = {k: statistics.mean(s["gpu_ms_" + k] for s in stage) for k in keys}
-    flops = _algorithmic(stage[-1], w["p"], n)
-    dominant = max((k for k in flops), key=lambda k: mean_stage[k])
+    # dominant kernel: the M2L translation products (k_zgemm_res), timed by the
+    # library's CUDA events around its launches on the evaluation's stream
+    gemm_ms = statistics.mean(s["gpu_ms_m2l_gemm"] for s in stage)
+    gemm_flops = stage[-1]["m2l_gemm_flops"]
     peak = pkg.measure_fp64_peak() / 1e3
-    achieved = flops[dominant] / (mean_stage[dominant] * 1e-3) / 1e12
+    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get(WORKLOAD["name"])
     result = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -255,9 +250,11 @@ def main():
         "clocks": _clock_summary(clock_path),
         "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": "FP64 FMA throughput measured on this GPU by the library's probe"},
+        "roofline": {"bound": "alu", "kernel": "k_zgemm_res", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "per": "the M2L product launches of one evaluation (free-space and reaction classes)",
+                     "kernel_ms": gemm_ms, "algorithmic_tflop": gemm_flops / 1e12,
+                     "peak_source": "FP64 FMA throughput measured on this GPU by the library's probe (of measured)"},
         "stage_ms": mean_stage,
         "cold_first_eval": cold_info,
         "counts": {k: stage[-1][k] for k in ("n_components", "n_boxes", "n_v_pairs", "n_v_pairs_reac", "n_free_pairs",

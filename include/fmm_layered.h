@@ -79,6 +79,11 @@ typedef struct {
   long   n_launches;       /* kernels of this library launched by the last
                               evaluation (launches inside CUB's sort and scan
                               calls not included)                            */
+  double gpu_ms_m2l_gemm;  /* device time of the M2L translation products
+                              alone (CUDA events around those launches)      */
+  double m2l_gemm_flops;   /* their algorithmic flops: 8 per complex
+                              multiply-add of operator entry and expansion
+                              coefficient over all V-list translations       */
 } fmm_stats_t;
 
 /*

@@ -25,7 +25,8 @@ void launch_reac_split(int p, const cplx* full, cplx* out, cudaStream_t st);
 void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
                   const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
                   const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
-                  const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st);
+                  const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
+                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops);
 void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
                       int* err, cudaStream_t st);
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
@@ -232,7 +233,7 @@ extern "C" int fmm_layered_direct(fmm_layered_t* h, long ns, const double* src, 
 
 // ---------------------------------------------------------------- eval
 struct StageEvents {
-  cudaEvent_t ev[10];
+  cudaEvent_t ev[12];
   StageEvents() { for (auto& e : ev) cudaEventCreate(&e); }
   ~StageEvents() { for (auto& e : ev) cudaEventDestroy(e); }
   void mark(int i, cudaStream_t st) { cudaEventRecord(ev[i], st); }
@@ -566,8 +567,11 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   OI.reac_off = dtabs + 3 * nc * 23;
   OI.phase = h->tab.phase.as<cplx>();
   OI.cgs = dcg;
+  double gemm_flops = 0.0;
+  const bool gemm_ran = lo_all[nb] > 0;
   run_m2l_gemm(h, nb, (long)lo_all[nb], m2l_lvl, dsched, o_m2l, maxlev, B, OI, loff, ws.vi.as<int>(),
-               oc.free_buf.as<cplx>(), oc.rad_buf.as<cplx>(), oc.shift_buf.as<cplx>(), M, L, err, st);
+               oc.free_buf.as<cplx>(), oc.rad_buf.as<cplx>(), oc.shift_buf.as<cplx>(), M, L, err, st, E.ev[10],
+               E.ev[11], &gemm_flops);
   FMM_CHECK(cudaGetLastError());
   E.mark(4, st);
   long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;
@@ -621,6 +625,8 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.gpu_ms_near_reac = E.ms(6, 7);
   h->stats.gpu_ms_sum = E.ms(7, 8);
   h->stats.gpu_ms_total = E.ms(0, 8);
+  h->stats.gpu_ms_m2l_gemm = gemm_ran ? E.ms(10, 11) : 0.0;
+  h->stats.m2l_gemm_flops = gemm_flops;
   h->stats.n_free_pairs = (long)hc[0];
   h->stats.n_reac_pairs = (long)hc[2];
   h->stats.n_reac_nodes = (long)hc[3];

@@ -308,7 +308,8 @@ static size_t gemm_smem_max(int R) {
 void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
                   const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
                   const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
-                  const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st) {
+                  const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
+                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops) {
   Workspace& ws = h->ws;
   const int p = h->p, P = (p + 1) * (p + 1);
   const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;
@@ -355,6 +356,7 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     // batches and tiles
     std::vector<GemmBatch> bat;
     long k0 = 0;
+    double macs = 0.0;       // complex multiply-adds of the translations (operator entries x columns)
     for (int r = 0; r < nruns; ++r) {
       long off = (long)(hk[r] >> 1);
       bool reac = hk[r] & 1;
@@ -375,9 +377,11 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
       };
       if (!reac) {
         add(off, P, 0);
+        macs += (double)K * P * P;
       } else {
         add(off, np, 0);
         if (nm) add(off + (long)np * np, nm, np);
+        macs += (double)K * ((double)np * np + (double)nm * nm);
       }
       k0 += K;
     }
@@ -401,12 +405,15 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     auto smem_of = [&](int R) { return gemm_smem_max(R); };
     size_t smax = std::max(smem_of(P), std::max(smem_of(np), nm ? smem_of(nm) : (size_t)0));
     cudaFuncSetAttribute(k_zgemm_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    *gemm_flops = 8.0 * macs;
+    FMM_CHECK(cudaEventRecord(gemm0, st));
     if (!bfree.empty())
       LAUNCH(k_zgemm_res<<<(unsigned)bfree.size(), 128, smem_of(P), st>>>(dbat, free_ops, ws.g_Y.as<cplx>(),
                                                                           ws.g_Z.as<cplx>()));
     if (!breac.empty())
       LAUNCH(k_zgemm_res<<<(unsigned)breac.size(), 128, std::max(smem_of(np), nm ? smem_of(nm) : (size_t)0), st>>>(
           dbat + bfree.size(), reac_ops, ws.g_Y.as<cplx>(), ws.g_Z.as<cplx>()));
+    FMM_CHECK(cudaEventRecord(gemm1, st));
     FMM_CHECK(cudaGetLastError());
     // per-target sums (all levels)
     for (int l = 2; l <= maxlev; ++l)

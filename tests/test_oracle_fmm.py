@@ -193,7 +193,7 @@ def test_fmm_converges_to_direct_sum():
 
 def test_fmm_identical_layers_equals_free_space():
     # All layers identical: the layered FMM equals the free-space direct sum
-    # over all sources (the benchmark spec bullet 1).
+    # over all sources (Sec. 3.1: with equal media there is no reflection).
     rng = np.random.default_rng(7)
     src = rng.uniform(-1, 1, (160, 3))
     src[:80, 2] = rng.uniform(0.1, 1.1, 80)

@@ -48,7 +48,7 @@ def test_printed_three_layer_densities():
 def test_identical_layers_give_free_space():
     # All layers equal: no reflection; the only reaction component that
     # survives is the transmitted wave, equal to the free-space wave
-    # (the benchmark spec bullet 1; Sec. 3.1 eq. domaingreenfn).
+    # (Sec. 3.1 eq. domaingreenfn).
     med = Medium([1.1, 1.1, 1.1], [0.0, -1.0], eps=[2.0, 2.0, 2.0])
     kr = np.array([0.2 - 0.3j, 1.5 - 0.3j, 4.0 - 0.3j])
     for lp in range(3):
