@@ -48,6 +48,11 @@ extern "C" {
                                  4 pi / (i k_l): the paper's h_0 normalization
                                  with the factor i k_l / 4 pi omitted (eq.
                                  totalinteraction)                             */
+#define FMM_MIXED        2u   /* M2L translations on the tensor cores: FP16
+                                 hi/lo split operands with power-of-two
+                                 scaling, FP32 accumulation (3 products); every
+                                 other stage stays FP64.  Relative error of the
+                                 potentials below 1e-5.                        */
 
 typedef struct fmm_layered fmm_layered_t;
 
@@ -95,7 +100,7 @@ typedef struct {
  *               condition [eps du/dz] = 0 (host; NULL means all 1)
  *   p           expansion order, 1 <= p <= 16 (terms n = 0..p)
  *   leaf        maximum number of sources or targets in a leaf box, >= 1
- *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER
+ *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER | FMM_MIXED
  *   out         receives the handle (NULL on failure)
  * Builds the contour quadrature rule and the reaction densities sigma at its
  * nodes on the current device.  Returns FMM_ERR_ARG for invalid input.

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libfmmlayered.so")
 
 FMM_PLAIN_FP64 = 0
 FMM_NORM_PAPER = 1
+FMM_MIXED = 2
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "point on an interface", -3: "non-finite input",
           -4: "CUDA error", -5: "out of device memory", -6: "timeout", -7: "unsupported"}
@@ -134,9 +135,11 @@ def _ptr(a):
 
 class LayeredFMM:
     """Solver for one layered medium (Sec. 3.1): wave numbers k (top to bottom),
-    interfaces d (descending), material coefficients eps, order p, leaf size."""
+    interfaces d (descending), material coefficients eps, order p, leaf size.
+    mixed=True runs the M2L translations on the tensor cores (FP16 hi/lo
+    operands, FP32 accumulation); every other stage stays FP64."""
 
-    def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False):
+    def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False, mixed=False):
         L = lib()
         self.k = np.ascontiguousarray(k, dtype=np.float64)
         self.d = np.ascontiguousarray(d, dtype=np.float64)
@@ -145,7 +148,8 @@ class LayeredFMM:
         h = ctypes.c_void_p()
         rc = L.fmm_layered_create(len(self.k), _ptr(self.k), _ptr(self.d) if len(self.d) else None,
                                   _ptr(self.eps), self.p, self.leaf,
-                                  FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64, ctypes.byref(h))
+                                  (FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64) | (FMM_MIXED if mixed else 0),
+                                  ctypes.byref(h))
         if rc != 0:
             raise FmmError(rc, L.fmm_layered_last_error(None).decode())
         self.h = h

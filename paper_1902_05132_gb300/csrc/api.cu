@@ -26,7 +26,7 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
                   const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
                   const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
                   const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
-                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops);
+                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh);
 void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
                       int* err, cudaStream_t st);
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
@@ -162,7 +162,9 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
                    &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
                    &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.cub_tmp};
   for (DevBuf* b : wsb) b->release();
-  DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat};
+  DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
+                  &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items,
+                  &h->tc.bbuf, &h->tc.sbuf};
   for (DevBuf* b : gb) b->release();
   h->cache.free_buf.release();
   h->cache.shift_buf.release();
@@ -571,7 +573,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   const bool gemm_ran = lo_all[nb] > 0;
   run_m2l_gemm(h, nb, (long)lo_all[nb], m2l_lvl, dsched, o_m2l, maxlev, B, OI, loff, ws.vi.as<int>(),
                oc.free_buf.as<cplx>(), oc.rad_buf.as<cplx>(), oc.shift_buf.as<cplx>(), M, L, err, st, E.ev[10],
-               E.ev[11], &gemm_flops);
+               E.ev[11], &gemm_flops, cg);
   FMM_CHECK(cudaGetLastError());
   E.mark(4, st);
   long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;
@@ -614,6 +616,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaMemcpyAsync(hc, counters, 32, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
+  if (herr & 16) throw FmmError(FMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait on an mbarrier expired");
   if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair without an operator");
   h->stats.ms_eval = ms_since(t2);
   h->stats.gpu_ms_tree = E.ms(0, 1);

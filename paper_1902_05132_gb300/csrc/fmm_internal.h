@@ -114,6 +114,8 @@ struct Workspace {
   DevBuf phi;           // per component-target results (sorted order)
   // M2L as batched GEMMs
   DevBuf g_owner, g_keys, g_vals, g_inv, g_Y, g_Z, g_runs, g_bat;
+  // tensor-core M2L (mixed precision): run tables, operand tiles, scales, work items
+  DevBuf tc_runs, tc_jobs, tc_a, tc_sig, tc_parts, tc_items;
   DevBuf out_tmp;
   DevBuf cub_tmp;
 };
@@ -135,6 +137,16 @@ struct OpCache {
   }
 };
 
+// FP16 hi/lo copies of translation operators for the tensor-core M2L, keyed
+// by (FP64 operator offset, reaction, basis block, first output row).
+struct TcOpRef { long dst_off, scale_off; int N_pad, R16, RB, r0; };
+struct TcCache {
+  DevBuf bbuf, sbuf;                      // operator tiles (bytes), row scales (doubles)
+  long b_used = 0, s_used = 0, b_used_done = 0, s_done = 0;
+  std::map<std::tuple<long, int, int, int>, TcOpRef> ops;
+  std::vector<bool> pending_reac;
+};
+
 struct fmm_layered {
   int L1 = 0;               // number of layers
   std::vector<double> k, d, eps;
@@ -146,6 +158,7 @@ struct fmm_layered {
   Tables tab;
   Workspace ws;
   OpCache cache;
+  TcCache tc;
   fmm_stats_t stats{};
   std::string err;
   // state of the last evaluation (for export)
@@ -163,6 +176,11 @@ struct fmm_layered {
 // batched call, each evaluated by its own host thread, count their own.
 extern thread_local long g_fmm_launches;
 #define LAUNCH(...) do { ++g_fmm_launches; __VA_ARGS__; } while (0)
+
+inline void* tc_need(DevBuf& b, size_t n) {
+  b.ensure(n ? n : 1);
+  return b.ptr;
+}
 
 // ---- plain-data structures passed to kernels
 struct SepJob { double b[3]; double k; int kind; long out_off; };

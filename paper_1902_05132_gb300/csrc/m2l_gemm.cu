@@ -303,13 +303,19 @@ static size_t gemm_smem_max(int R) {
   return m;
 }
 
+void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned long long>& hk,
+                const std::vector<int>& hc, const int* perm, const int* owner, const int* vidx, BoxGeom B,
+                OpIndex OI, const std::vector<CompGeom>& cgh, const cplx* free_ops, const cplx* reac_ops,
+                const cplx* M, cplx* Z, int* err, cudaStream_t st, cudaEvent_t gemm0, cudaEvent_t gemm1,
+                double* gemm_flops);
+
 // Host driver: all V pairs of all levels.  L receives the M2L part for every
 // box with targets at level >= 2; then L2L level by level.
 void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
                   const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
                   const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
                   const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
-                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops) {
+                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh) {
   Workspace& ws = h->ws;
   const int p = h->p, P = (p + 1) * (p + 1);
   const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;
@@ -318,7 +324,8 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     ws.g_keys.ensure(8 * nv * 2);
     ws.g_vals.ensure(4 * nv * 2);
     ws.g_inv.ensure(4 * nv);
-    ws.g_Y.ensure(sizeof(cplx) * (size_t)nv * P);
+    const bool mixed = (h->flags & FMM_MIXED) != 0;
+    if (!mixed) ws.g_Y.ensure(sizeof(cplx) * (size_t)nv * P);
     ws.g_Z.ensure(sizeof(cplx) * (size_t)nv * P);
     int* owner = ws.g_owner.as<int>();
     unsigned long long* keys = ws.g_keys.as<unsigned long long>();
@@ -349,6 +356,11 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     std::vector<int> hc(nruns);
     FMM_CHECK(cudaMemcpyAsync(hk.data(), ukeys, 8 * (size_t)nruns, cudaMemcpyDeviceToHost, st));
     FMM_CHECK(cudaMemcpyAsync(hc.data(), counts, 4 * (size_t)nruns, cudaMemcpyDeviceToHost, st));
+    if (mixed) {
+      FMM_CHECK(cudaStreamSynchronize(st));
+      run_m2l_tc(h, nv, nruns, hk, hc, perm, owner, vidx, B, OI, cgh, free_ops, reac_ops, M, ws.g_Z.as<cplx>(),
+                 err, st, gemm0, gemm1, gemm_flops);
+    } else {
     // gather the columns
     LAUNCH(k_m2l_gather<<<(unsigned)nv, 64, sizeof(cplx) * P, st>>>(nv, p, perm, owner, vidx, B, OI, M,
                                                                    ws.g_Y.as<cplx>()));
@@ -415,6 +427,7 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
           dbat + bfree.size(), reac_ops, ws.g_Y.as<cplx>(), ws.g_Z.as<cplx>()));
     FMM_CHECK(cudaEventRecord(gemm1, st));
     FMM_CHECK(cudaGetLastError());
+    }
     // per-target sums (all levels)
     for (int l = 2; l <= maxlev; ++l)
       if (!m2l_lvl[l].empty())
