@@ -81,6 +81,17 @@ def _clock_summary(path):
             "samples": len(sm)}
 
 
+def _tensor_peak():
+    """Dense FP16 tensor peak: the measured bf16 burst figure of this machine
+    (FP16 and BF16 run at the same nominal rate), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured bf16 dense burst x 1 (fp16 nominal ratio) (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 dense (of fallback)"
+
+
 def cpu_oracle_sample(n_targets, seed=0):
     """Time the oracle (as it stands: FP64 direct sum with Sommerfeld
     quadrature) for n_targets sampled targets of the full workload against
@@ -260,6 +271,42 @@ def main():
         "counts": {k: stage[-1][k] for k in ("n_components", "n_boxes", "n_v_pairs", "n_v_pairs_reac", "n_free_pairs",
                                              "n_reac_pairs", "n_reac_nodes", "n_reac_classes", "n_reac_T_nodes")},
     }
+    # mixed-precision form on the same workload: M2L on the tensor cores
+    ref_out = out.clone()
+    mixed = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], mixed=True)
+    out_m = torch.empty_like(out)
+    for _ in range(max(3, args.warmup)):
+        mixed.eval(src, q, tgt, out=out_m)
+    mms, mst = [], []
+    torch.cuda.nvtx.range_push("timed_mixed")
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mixed.eval(src, q, tgt, out=out_m)
+        e1.record(stream)
+        e1.synchronize()
+        mms.append(e0.elapsed_time(e1))
+        mst.append(mixed.stats())
+    torch.cuda.nvtx.range_pop()
+    m_ms = statistics.mean(mms)
+    tc_ms = statistics.mean(s["gpu_ms_m2l_gemm"] for s in mst)
+    tc_flops = mst[-1]["m2l_tensor_flops"]
+    bf16_peak, peak_src = _tensor_peak()
+    tc_achieved = tc_flops / (tc_ms * 1e-3) / 1e12
+    err_m = float(torch.linalg.vector_norm(out_m - ref_out) / torch.linalg.vector_norm(ref_out))
+    result["mixed"] = {
+        "value": ws * n / (m_ms * 1e-3), "unit": "particles/s", "ms_per_step": m_ms,
+        "rel_l2_vs_fp64_path": err_m, "dtype": "f16 hi/lo -> f32 (M2L), f64 elsewhere",
+        "stage_ms": {k: statistics.mean(s["gpu_ms_" + k] for s in mst) for k in keys},
+        "roofline": {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": tc_achieved, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": tc_achieved / bf16_peak, "traffic": NCU_TRAFFIC.get("mixed"),
+                     "kernel_ms": tc_ms, "executed_tflop": tc_flops / 1e12,
+                     "algorithmic_fp64_equiv_tflop": mst[-1]["m2l_gemm_flops"] / 1e12,
+                     "peak_source": peak_src},
+    }
+    mixed.close()
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         n_sample = 6
         v, sec = cpu_oracle_sample(n_sample)

@@ -89,6 +89,9 @@ typedef struct {
   double m2l_gemm_flops;   /* their algorithmic flops: 8 per complex
                               multiply-add of operator entry and expansion
                               coefficient over all V-list translations       */
+  double m2l_tensor_flops; /* FMM_MIXED: flops the tensor cores executed for
+                              them (3 real products per tile, padding
+                              included); 0 in the FP64 path                  */
 } fmm_stats_t;
 
 /*

@@ -162,6 +162,23 @@ __device__ inline void split_half(double v, __half& hi, __half& lo) {
   hi = __float2half_rn((float)v);
   lo = __float2half_rn((float)(v - (double)__half2float(hi)));
 }
+// Same split from an FP32 value (x - hi is exact in FP32): no FP64 arithmetic.
+__device__ inline void split_half_f(float x, __half& hi, __half& lo) {
+  hi = __float2half_rn(x);
+  lo = __float2half_rn(x - __half2float(hi));
+}
+// f * 2^e as a double, built from the bit pattern with integer arithmetic only
+// (exact; FP32 zeros and subnormals -- below 2^-126 of the O(1) scaled
+// accumulators -- give 0).
+__device__ inline double f32_scaled_to_f64(float f, int e) {
+  const uint32_t u = __float_as_uint(f);
+  const int ex = (int)((u >> 23) & 0xFFu);
+  if (ex == 0) return 0.0;
+  const int dex = ex - 127 + 1023 + e;
+  if (ex == 255 || dex <= 0 || dex >= 2047) return ldexp((double)f, e);
+  const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)dex << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
 
 __device__ inline double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -180,14 +197,14 @@ __device__ inline double block_max(double v, double* red) {
 struct TcOpJob {
   long src_off;      // FP64 operator, input-major: entry (out r, in c) at src_off + c * R_full + r
   long dst_off;      // bytes: [hi/lo][Kc][N_pad rows][128 B]
-  long scale_off;    // doubles: rscale[r], r < RB
+  long scale_off;    // ints: output exponent shift - E_out(n(r)), r < RB
   int R_full, C, r0, RB, R16, N_pad, Kc, basis;
   double kin, kout, w;
 };
 
 // Scaled, split, swizzled FP16 copy of an operator sub-block (one CTA each).
 __global__ void __launch_bounds__(256) k_tc_prep_ops(const TcOpJob* __restrict__ jobs, const cplx* __restrict__ ops,
-                                                     unsigned char* __restrict__ dst, double* __restrict__ rscale) {
+                                                     unsigned char* __restrict__ dst, int* __restrict__ rexp) {
   const TcOpJob jb = jobs[blockIdx.x];
   __shared__ int Eout[128];
   __shared__ int Ein[FMM_MAXP * FMM_MAXP + 2 * FMM_MAXP + 1];
@@ -235,14 +252,14 @@ __global__ void __launch_bounds__(256) k_tc_prep_ops(const TcOpJob* __restrict__
     *(uint4*)(D + off) = *(const uint4*)hv;
     *(uint4*)(D + half_bytes + off) = *(const uint4*)lv;
   }
-  for (int r = threadIdx.x; r < jb.RB; r += blockDim.x) rscale[jb.scale_off + r] = ldexp(1.0, shift - Eout[r]);
+  for (int r = threadIdx.x; r < jb.RB; r += blockDim.x) rexp[jb.scale_off + r] = shift - Eout[r];
 }
 
 // One contraction part of a run (class): free operator, or the plus / minus
 // block of a reaction operator.
 struct TcPart {
   long a_off;        // bytes of tile 0: tiles of [hi/lo][Kc][128 rows][128 B]
-  long sig_off;      // doubles: 2^{e_k} per tile row
+  long sig_off;      // ints: column exponent e_k per tile row
   int C, in_off, Kc, basis;
 };
 
@@ -252,7 +269,7 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
                                                   BoxGeom B, OpIndex OI, const cplx* __restrict__ M,
                                                   const int* __restrict__ run_start, int nruns,
                                                   const int* __restrict__ run_part, const TcPart* __restrict__ parts,
-                                                  unsigned char* __restrict__ Abuf, double* __restrict__ isig) {
+                                                  unsigned char* __restrict__ Abuf, int* __restrict__ isig) {
   const int P = (p + 1) * (p + 1);
   long k = blockIdx.x;
   if (k >= nv) return;
@@ -272,6 +289,8 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
   const CompGeom& cg = OI.cgs[comp];
   extern __shared__ cplx ys[];                 // [2 P]: rotated column, then its symmetric-basis form
   __shared__ double red[2];
+  __shared__ double pw[FMM_MAXP + 1];          // 2^{-E_in(n)} of this box size and wave number
+  __shared__ double sc[(FMM_MAXP + 1) * (FMM_MAXP + 1)];   // per contraction entry of the current part
   cplx* xs = ys + P;
   const cplx* Ms = M + (long)S * P;
   if (cg.kind == CK_FREE) {
@@ -302,16 +321,19 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
       ys[a] = u;
     }
   }
-  __syncthreads();
   const double w = cg.h2 / (double)(1 << lev);
+  for (int n = threadIdx.x; n <= p; n += blockDim.x) pw[n] = ldexp(1.0, -deg_exp(cg.ks, w, n));
+  __syncthreads();
   for (int q = 0; q < 2; ++q) {
     int pi = run_part[2 * run + q];
     if (pi < 0) continue;
     const TcPart pt = parts[pi];
     double mx = 0.0;
     for (int c = threadIdx.x; c < pt.C; c += blockDim.x) {
+      double f = pw[deg_of(pt.basis, c)];
+      sc[c] = f;
       cplx v = ys[pt.in_off + c];
-      mx = fmax(mx, ldexp(fmax(fabs(v.x), fabs(v.y)), -deg_exp(cg.ks, w, deg_of(pt.basis, c))));
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)) * f);
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     __syncthreads();
@@ -320,6 +342,9 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
     mx = fmax(red[0], red[1]);
     int ek = 0;
     if (mx > 0.0) frexp(mx, &ek);             // scaled entries below 1
+    const double sk = ldexp(1.0, -ek);
+    for (int c = threadIdx.x; c < pt.C; c += blockDim.x) sc[c] *= sk;
+    __syncthreads();
     const int units = pt.Kc * (kChunk / 8);
     const long tile_bytes = 2L * pt.Kc * kTileM * kRowBytes, half_bytes = (long)pt.Kc * kTileM * kRowBytes;
     const int tile = m / kTileM, row = m % kTileM;
@@ -330,20 +355,20 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         int ji = chunk * kChunk + uu * 8 + t;
-        double v = 0.0;
+        float v = 0.0f;
         if (ji < 2 * pt.C) {
           bool re = ji < pt.C;
           int c = re ? ji : ji - pt.C;
           cplx y = ys[pt.in_off + c];
-          v = ldexp(re ? y.x : y.y, -deg_exp(cg.ks, w, deg_of(pt.basis, c)) - ek);
+          v = (float)((re ? y.x : y.y) * sc[c]);   // power-of-two scale: exact before the rounding to FP32
         }
-        split_half(v, hv[t], lv[t]);
+        split_half_f(v, hv[t], lv[t]);
       }
       long off = (long)chunk * kTileM * kRowBytes + swz_unit(row, uu);
       *(uint4*)(Tb + off) = *(const uint4*)hv;
       *(uint4*)(Tb + half_bytes + off) = *(const uint4*)lv;
     }
-    if (threadIdx.x == 0) isig[pt.sig_off + m] = ldexp(1.0, ek);
+    if (threadIdx.x == 0) isig[pt.sig_off + m] = ek;
     // the last pair of the run clears the unused rows of its last tile
     if (m == K - 1) {
       const int pad = kTileM - 1 - row;
@@ -353,7 +378,7 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
         *(uint4*)(Tb + off) = make_uint4(0, 0, 0, 0);
         *(uint4*)(Tb + half_bytes + off) = make_uint4(0, 0, 0, 0);
       }
-      for (int f = threadIdx.x; f < pad; f += blockDim.x) isig[pt.sig_off + m + 1 + f] = 0.0;
+      for (int f = threadIdx.x; f < pad; f += blockDim.x) isig[pt.sig_off + m + 1 + f] = 0;
     }
     __syncthreads();
   }
@@ -363,7 +388,7 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
 struct TcItem {
   long a_off;        // bytes: this tile's [hi/lo][Kc][128][128 B]
   long b_off;        // bytes: operator sub-block [hi/lo][Kc][N_pad][128 B]
-  long scale_off;    // rscale of the sub-block's rows
+  long scale_off;    // output exponents of the sub-block's rows
   long sig_off;      // isig of this tile's rows
   long z_row0;       // translated-column index (sorted pair) of tile row 0
   int rows;          // valid rows of the tile
@@ -374,7 +399,7 @@ struct TcItem {
 // D[128 x N_pad] = A_tile (128 x 64 Kc) * B^T in tensor memory, then Z.
 __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items, const unsigned char* __restrict__ Abuf,
                                                const unsigned char* __restrict__ Bbuf,
-                                               const double* __restrict__ rscale, const double* __restrict__ isig,
+                                               const int* __restrict__ rexp, const int* __restrict__ isig,
                                                cplx* __restrict__ Z, int P, int* __restrict__ err) {
   const TcItem it = items[blockIdx.x];
   extern __shared__ unsigned char smraw[];
@@ -461,7 +486,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
   if (!abort_sh) {
     const int m = warp * 32 + lane;               // tile row = tensor-memory lane
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    const double sg = (m < it.rows) ? isig[it.sig_off + m] : 0.0;
+    const int ek = (m < it.rows) ? isig[it.sig_off + m] : 0;
     cplx* zr = Z + (it.z_row0 + m) * (long)P + it.z_col0;
     for (int r0 = 0; r0 < it.R16; r0 += 16) {
       float re[16], im[16];
@@ -472,8 +497,8 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
         for (int j = 0; j < 16; ++j) {
           int r = r0 + j;
           if (r < it.RB) {
-            double sc = rscale[it.scale_off + r] * sg;
-            zr[r] = C((double)re[j] * sc, (double)im[j] * sc);
+            const int e = rexp[it.scale_off + r] + ek;
+            zr[r] = C(f32_scaled_to_f64(re[j], e), f32_scaled_to_f64(im[j], e));
           }
         }
       }
@@ -606,10 +631,13 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
     }
   }
   *gemm_flops = 8.0 * macs;
+  double tflops = 0.0;
+  for (const TcItem& t : items) tflops += 3.0 * 2.0 * kTileM * t.N_pad * (double)(t.Kc * kChunk);
+  h->stats.m2l_tensor_flops = tflops;
   // operator conversions (new classes only)
   if (!jobs.empty()) {
     tc.bbuf.grow_keep(std::max<size_t>((size_t)tc.b_used, 256), (size_t)(tc.b_used_done), st);
-    tc.sbuf.grow_keep(sizeof(double) * std::max<size_t>((size_t)tc.s_used, 32), sizeof(double) * (size_t)tc.s_done, st);
+    tc.sbuf.grow_keep(sizeof(int) * std::max<size_t>((size_t)tc.s_used, 32), sizeof(int) * (size_t)tc.s_done, st);
     // free-space and reaction operators live in different FP64 buffers: two launches
     std::vector<TcOpJob> jf, jr;
     for (size_t i = 0; i < jobs.size(); ++i) (tc.pending_reac[i] ? jr : jf).push_back(jobs[i]);
@@ -620,10 +648,10 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
     FMM_CHECK(cudaMemcpyAsync(dj, all.data(), sizeof(TcOpJob) * all.size(), cudaMemcpyHostToDevice, st));
     if (!jf.empty())
       LAUNCH(k_tc_prep_ops<<<(unsigned)jf.size(), 256, 0, st>>>(dj, free_ops, tc.bbuf.as<unsigned char>(),
-                                                               tc.sbuf.as<double>()));
+                                                               tc.sbuf.as<int>()));
     if (!jr.empty())
       LAUNCH(k_tc_prep_ops<<<(unsigned)jr.size(), 256, 0, st>>>(dj + jf.size(), reac_ops,
-                                                               tc.bbuf.as<unsigned char>(), tc.sbuf.as<double>()));
+                                                               tc.bbuf.as<unsigned char>(), tc.sbuf.as<int>()));
     FMM_CHECK(cudaGetLastError());
     tc.b_used_done = tc.b_used;
     tc.s_done = tc.s_used;
@@ -631,7 +659,7 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   }
   // A tiles
   unsigned char* Abuf = (unsigned char*)tc_need(ws.tc_a, (size_t)a_bytes_total + 256);
-  double* isig = (double*)tc_need(ws.tc_sig, sizeof(double) * (size_t)sig_total + 64);
+  int* isig = (int*)tc_need(ws.tc_sig, sizeof(int) * (size_t)sig_total + 64);
   TcPart* dparts = (TcPart*)tc_need(ws.tc_parts, sizeof(TcPart) * parts.size() + 64);
   FMM_CHECK(cudaMemcpyAsync(dparts, parts.data(), sizeof(TcPart) * parts.size(), cudaMemcpyHostToDevice, st));
   FMM_CHECK(cudaMemcpyAsync(d_part, run_part.data(), sizeof(int) * run_part.size(), cudaMemcpyHostToDevice, st));
@@ -647,7 +675,7 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   FMM_CHECK(cudaEventRecord(gemm0, st));
   if (!items.empty())
     LAUNCH(k_m2l_tc<<<(unsigned)items.size(), 128, smem, st>>>(ditems, Abuf, tc.bbuf.as<unsigned char>(),
-                                                              tc.sbuf.as<double>(), isig, Z, P, err));
+                                                              tc.sbuf.as<int>(), isig, Z, P, err));
   FMM_CHECK(cudaEventRecord(gemm1, st));
   FMM_CHECK(cudaGetLastError());
   FMM_CHECK(cudaStreamSynchronize(st));       // host tables above go out of scope

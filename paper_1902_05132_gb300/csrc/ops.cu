@@ -396,51 +396,117 @@ __device__ inline void box_center(const CompGeom& cg, int level, const int* coor
   for (int a = 0; a < 3; ++a) c[a] = cg.lo[a] + (coord[a] + 0.5) * w;
 }
 
-// point values for expansion: out[(n,m)] = 4 pi j_n(k r) conj(Y_n^m) (conj = true)
-// or j_n(k r) Y_n^m (conj = false)
-__device__ inline void regular_values(int p, double k, double dx, double dy, double dz, bool conj_y,
-                                      double scale, cplx* out) {
-  double r, ct, st, ph;
-  to_sph(dx, dy, dz, r, ct, st, ph);
-  double jn[FMM_MAXP + 1];
-  sph_jn(p, k * r, jn);
-  double Pa[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
-  phat_real(p, ct, st, Pa);
-  for (int m = 0; m <= p; ++m) {
-    double s, c;
-    sincos(m * ph, &s, &c);
-    if (conj_y) s = -s;
-    for (int n = m; n <= p; ++n) {
-      double v = scale * jn[n] * Pa[PH(n, m)];
-      out[NM(n, m)] = C(v * c, v * s);
-      if (m) {
-        double sg = (m & 1) ? -1.0 : 1.0;
-        out[NM(n, -m)] = C(sg * v * c, -sg * v * s);
-      }
+// Recurrence coefficients of the normalized Legendre functions (the same
+// a_nm, b_nm as phat_real) and the diagonal factors
+// P^_m^m = c_diag[m] s^m, tabulated once so that the per-particle passes do
+// no FP64 square roots or divisions.  Index n(n+1)/2 + m, n <= FMM_MAXP.
+__constant__ double c_reca[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
+__constant__ double c_recb[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
+__constant__ double c_diag[FMM_MAXP + 1];
+
+void init_legendre_tables() {
+  const int NT = (FMM_MAXP + 1) * (FMM_MAXP + 2) / 2;
+  std::vector<double> a(NT, 0.0), b(NT, 0.0), dg(FMM_MAXP + 1);
+  for (int n = 0; n <= FMM_MAXP; ++n)
+    for (int m = 0; m < n; ++m) {
+      a[n * (n + 1) / 2 + m] = rec_a(n, m);
+      b[n * (n + 1) / 2 + m] = rec_b(n, m);
     }
-  }
+  dg[0] = 0.28209479177387814;
+  for (int m = 1; m <= FMM_MAXP; ++m) dg[m] = dg[m - 1] * sqrt((2.0 * m + 1.0) / (2.0 * m));
+  FMM_CHECK(cudaMemcpyToSymbol(c_reca, a.data(), sizeof(double) * NT));
+  FMM_CHECK(cudaMemcpyToSymbol(c_recb, b.data(), sizeof(double) * NT));
+  FMM_CHECK(cudaMemcpyToSymbol(c_diag, dg.data(), sizeof(double) * (FMM_MAXP + 1)));
 }
 
-// One CTA per source leaf: threads form the values of up to `chunk` sources
-// at a time in shared memory, then each thread sums its coefficients.
-__global__ void k_p2m(int p, int chunk, const int* __restrict__ leaves, BoxGeom B, const CompGeom* __restrict__ cgs,
-                      const double* __restrict__ spos, const cplx* __restrict__ sq, cplx* __restrict__ M) {
+// j_n(x), n = 0..p, as sph_jn but multiplying by 1/x instead of dividing.
+__device__ inline void sph_jn_fast(int p, double x, double* j) {
+  if (x == 0.0) {
+    j[0] = 1.0;
+    for (int n = 1; n <= p; ++n) j[n] = 0.0;
+    return;
+  }
+  double s, c;
+  sincos(x, &s, &c);
+  const double ix = 1.0 / x;
+  double j0 = (x < 1e-4) ? 1.0 - x * x / 6.0 : s * ix;
+  if (x > (double)p) {
+    j[0] = j0;
+    if (p >= 1) j[1] = (s * ix - c) * ix;
+    for (int n = 1; n < p; ++n) j[n + 1] = (2 * n + 1) * ix * j[n] - j[n - 1];
+    return;
+  }
+  int N = p + 20 + (int)x;
+  double f1 = 0.0, f0 = 1e-250;
+  for (int n = N; n >= 1; --n) {
+    double fm = (2 * n + 1) * ix * f0 - f1;
+    f1 = f0;
+    f0 = fm;
+    if (n - 1 <= p) j[n - 1] = f0;
+    if (fabs(f0) > 1e200) {
+      f0 *= 1e-200; f1 *= 1e-200;
+      for (int m = n - 1; m <= p; ++m) j[m] *= 1e-200;
+    }
+  }
+  double sc = j0 / j[0];
+  for (int n = 0; n <= p; ++n) j[n] *= sc;
+}
+
+// One CTA per source leaf.  For a chunk of sources: one thread per source
+// forms r, angles and j_n(k r); then one thread per (source, order m) runs
+// the Legendre recurrence of column m and writes the 4 pi q j_n conj(Y_n^{+-m})
+// values; then each thread sums its coefficients over the chunk.
+__global__ void __launch_bounds__(128) k_p2m(int p, int chunk, const int* __restrict__ leaves, BoxGeom B,
+                                             const CompGeom* __restrict__ cgs, const double* __restrict__ spos,
+                                             const cplx* __restrict__ sq, cplx* __restrict__ M) {
   int b = leaves[blockIdx.x];
   const int P = (p + 1) * (p + 1);
   const CompGeom cg = cgs[B.comp[b]];
   double c[3];
   box_center(cg, B.lev[b], B.coord + 3 * b, c);
-  extern __shared__ cplx vals[];     // [chunk][P]
+  extern __shared__ cplx vals[];     // [chunk][P], then [chunk][p+1] j_n and [chunk][4] geometry
+  double* jn = (double*)(vals + (size_t)chunk * P);
+  double* geo = jn + (size_t)chunk * (p + 1);
   cplx acc[4] = {C(0, 0), C(0, 0), C(0, 0), C(0, 0)};
   for (int s0 = B.sb[b]; s0 < B.se[b]; s0 += chunk) {
     int ns = min(chunk, B.se[b] - s0);
     __syncthreads();
     for (int t = threadIdx.x; t < ns; t += blockDim.x) {
       int s = s0 + t;
-      regular_values(p, cg.ks, spos[3 * s] - c[0], spos[3 * s + 1] - c[1], spos[3 * s + 2] - c[2], true,
-                     4.0 * FMM_PI, vals + t * P);
-      cplx qv = sq[s];
-      for (int i = 0; i < P; ++i) vals[t * P + i] = cmul(vals[t * P + i], qv);
+      double r, ct, st, ph;
+      to_sph(spos[3 * s] - c[0], spos[3 * s + 1] - c[1], spos[3 * s + 2] - c[2], r, ct, st, ph);
+      sph_jn_fast(p, cg.ks * r, jn + t * (p + 1));
+      geo[4 * t] = ct;
+      geo[4 * t + 1] = st;
+      geo[4 * t + 2] = ph;
+    }
+    __syncthreads();
+    for (int item = threadIdx.x; item < ns * (p + 1); item += blockDim.x) {
+      const int t = item / (p + 1), m = item % (p + 1);
+      const double ct = geo[4 * t], st = geo[4 * t + 1], ph = geo[4 * t + 2];
+      const double* j = jn + t * (p + 1);
+      cplx qv = sq[s0 + t];
+      double sn, cs;
+      sincos(m * ph, &sn, &cs);
+      sn = -sn;                                    // conj(Y)
+      cplx e = cscale(cmul(C(cs, sn), qv), 4.0 * FMM_PI);
+      cplx e2 = cscale(cmul(C(cs, -sn), qv), 4.0 * FMM_PI * ((m & 1) ? -1.0 : 1.0));
+      double sm = 1.0;
+      for (int i = 0; i < m; ++i) sm *= st;
+      double p2 = 0.0, p1 = c_diag[m] * sm;
+      cplx* out = vals + t * P;
+      for (int n = m; n <= p; ++n) {
+        double pv;
+        if (n == m) pv = p1;
+        else {
+          pv = c_reca[n * (n + 1) / 2 + m] * ct * p1 - c_recb[n * (n + 1) / 2 + m] * p2;
+          p2 = p1;
+          p1 = pv;
+        }
+        double v = j[n] * pv;
+        out[n * n + n + m] = cscale(e, v);
+        if (m) out[n * n + n - m] = cscale(e2, v);
+      }
     }
     __syncthreads();
     for (int k = 0; k < 4; ++k) {
@@ -534,21 +600,28 @@ __global__ void k_l2p(int p, const int* __restrict__ leaves, BoxGeom B, const Co
     double r, ct, st, ph;
     to_sph(tpos[3 * t] - c[0], tpos[3 * t + 1] - c[1], tpos[3 * t + 2] - c[2], r, ct, st, ph);
     double jn[FMM_MAXP + 1];
-    sph_jn(p, cg.kt * r, jn);
-    double Pa[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
-    phat_real(p, ct, st, Pa);
+    sph_jn_fast(p, cg.kt * r, jn);
     cplx acc = C(0, 0);
+    double sm = 1.0;                  // st^m
     for (int m = 0; m <= p; ++m) {
       double s, cc;
       sincos(m * ph, &s, &cc);
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      // column m of the Legendre table by its recurrence (tabulated coefficients)
+      double p2 = 0.0, p1 = c_diag[m] * sm;
       for (int n = m; n <= p; ++n) {
-        double v = jn[n] * Pa[PH(n, m)];
-        cfma(acc, C(v * cc, v * s), Ls[NM(n, m)]);
-        if (m) {
-          double sg = (m & 1) ? -1.0 : 1.0;
-          cfma(acc, C(sg * v * cc, -sg * v * s), Ls[NM(n, -m)]);
+        double pv;
+        if (n == m) pv = p1;
+        else {
+          pv = c_reca[n * (n + 1) / 2 + m] * ct * p1 - c_recb[n * (n + 1) / 2 + m] * p2;
+          p2 = p1;
+          p1 = pv;
         }
+        double v = jn[n] * pv;
+        cfma(acc, C(v * cc, v * s), Ls[NM(n, m)]);
+        if (m) cfma(acc, C(sg * v * cc, -sg * v * s), Ls[NM(n, -m)]);
       }
+      sm *= st;
     }
     phi[t] = acc;
   }
@@ -598,8 +671,9 @@ void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const d
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
                 const cplx* sq, cplx* M, cudaStream_t st) {
   int P = (p + 1) * (p + 1);
-  int chunk = std::min(16, (int)((200 * 1024) / (sizeof(cplx) * P)));
-  size_t smem = sizeof(cplx) * chunk * P;
+  const size_t per = sizeof(cplx) * P + sizeof(double) * (p + 1 + 4);
+  int chunk = std::min(16, (int)((200 * 1024) / per));
+  size_t smem = per * chunk;
   cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (n) LAUNCH(k_p2m<<<n, 128, smem, st>>>(p, chunk, leaves, B, cgs, spos, sq, M));
 }
