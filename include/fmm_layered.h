@@ -50,9 +50,12 @@ extern "C" {
                                  totalinteraction)                             */
 #define FMM_MIXED        2u   /* M2L translations on the tensor cores: FP16
                                  hi/lo split operands with power-of-two
-                                 scaling, FP32 accumulation (3 products); every
-                                 other stage stays FP64.  Relative error of the
-                                 potentials below 1e-5.                        */
+                                 scaling, FP32 accumulation (3 products);
+                                 free-space near field in FP32 with a
+                                 compensated sum; expansions, operators, the
+                                 reaction near field and all sums over
+                                 translations stay FP64.  Relative error of
+                                 the potentials below 1e-5.                    */
 
 typedef struct fmm_layered fmm_layered_t;
 

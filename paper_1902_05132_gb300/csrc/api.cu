@@ -34,7 +34,8 @@ void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs,
 void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st);
 RuleView make_rule_view(const Rule& R, const cplx* coef);
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
-                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st);
+                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st,
+                 bool f32);
 double measure_fp64_peak_impl();
 void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
                    RuleView R, const cplx* coef_all, double* out, cudaStream_t st);
@@ -166,8 +167,8 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
                    &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.cub_tmp};
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
-                  &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items,
-                  &h->tc.bbuf, &h->tc.sbuf};
+                  &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,
+                  &h->tc.bbuf, &h->tc.sbuf, &h->tc.phase_f};
   for (DevBuf* b : gb) b->release();
   h->cache.free_buf.release();
   h->cache.shift_buf.release();
@@ -604,10 +605,11 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   unsigned long long* counters = need<unsigned long long>(ws.iota, 4);
   FMM_CHECK(cudaMemsetAsync(counters, 0, 32, st));
   launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
-              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st);
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st,
+              (h->flags & FMM_MIXED) != 0);
   E.mark(6, st);
   launch_near(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, make_rule_view(h->rule, coef),
-              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 2, st);
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 2, st, false);
   FMM_CHECK(cudaGetLastError());
   E.mark(7, st);
   for (int c = 0; c < nc; ++c)

@@ -115,7 +115,7 @@ struct Workspace {
   // M2L as batched GEMMs
   DevBuf g_owner, g_keys, g_vals, g_inv, g_Y, g_Z, g_runs, g_bat;
   // tensor-core M2L (mixed precision): run tables, operand tiles, scales, work items
-  DevBuf tc_runs, tc_jobs, tc_a, tc_sig, tc_parts, tc_items;
+  DevBuf tc_runs, tc_jobs, tc_a, tc_sig, tc_parts, tc_items, tc_etab;
   DevBuf out_tmp;
   DevBuf cub_tmp;
 };
@@ -141,7 +141,9 @@ struct OpCache {
 // by (FP64 operator offset, reaction, basis block, first output row).
 struct TcOpRef { long dst_off, scale_off; int N_pad, R16, RB, r0; };
 struct TcCache {
-  DevBuf bbuf, sbuf;                      // operator tiles (bytes), row scales (doubles)
+  DevBuf bbuf, sbuf;                      // operator tiles (bytes), row exponents (ints)
+  DevBuf phase_f;                         // FP32 copy of the rotation table e^{i m phi}
+  bool phase_ready = false;
   long b_used = 0, s_used = 0, b_used_done = 0, s_done = 0;
   std::map<std::tuple<long, int, int, int>, TcOpRef> ops;
   std::vector<bool> pending_reac;

@@ -132,20 +132,11 @@ __host__ __device__ inline uint32_t swz_unit(int row, int unit) {
   return (uint32_t)row * kRowBytes + (uint32_t)((unit ^ (row & 7)) * 16);
 }
 
-// floor(log2 s_n), s_n = (k rho)^n / (2n+1)!!, rho = (sqrt 3 / 2) w
-__device__ inline int deg_exp(double k, double w, int n) {
-  double x = k * 0.86602540378443864676 * w;
-  double s = 1.0;
-  for (int j = 1; j <= n; ++j) s *= x / (2.0 * j + 1.0);
-  int e;
-  frexp(s, &e);
-  return e - 1;
-}
 // degree of index i of a coefficient block: 0 full (n*n + n + m), 1 plus, 2 minus basis
 __device__ inline int deg_of(int basis, int i) {
   int n;
   if (basis == 0) {
-    n = (int)floor(sqrt((double)i));
+    n = (int)sqrtf((float)i);
     while ((n + 1) * (n + 1) <= i) ++n;
     while (n * n > i) --n;
   } else if (basis == 1) {
@@ -167,6 +158,34 @@ __device__ inline void split_half_f(float x, __half& hi, __half& lo) {
   hi = __float2half_rn(x);
   lo = __float2half_rn(x - __half2float(hi));
 }
+// x * 2^e rounded to FP32 (to nearest, ties to even), from the bit pattern
+// with integer arithmetic only.  Results below the FP32 normal range give a
+// signed 0: the callers scale each column so that its largest entry is near
+// 1, and such entries are then below 2^-126 of it.
+__device__ inline float d2f_scaled(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  const uint32_t sign = (uint32_t)(u >> 63) << 31;
+  if (ex == 0) return __uint_as_float(sign);
+  if (ex == 0x7FF) return (float)x;
+  int fe = ex - 1023 + e + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  uint32_t m23 = (uint32_t)((u & 0xFFFFFFFFFFFFFULL) >> 29);
+  const uint32_t rem = (uint32_t)(u & 0x1FFFFFFFULL);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) {
+    if (++m23 == 0x800000u) {
+      m23 = 0;
+      if (++fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    }
+  }
+  return __uint_as_float(sign | ((uint32_t)fe << 23) | m23);
+}
+// unbiased binary exponent of x (x != 0, normal): x in [2^E, 2^{E+1})
+__device__ inline int dexp_of(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+}
+
 // f * 2^e as a double, built from the bit pattern with integer arithmetic only
 // (exact; FP32 zeros and subnormals -- below 2^-126 of the O(1) scaled
 // accumulators -- give 0).
@@ -199,18 +218,20 @@ struct TcOpJob {
   long dst_off;      // bytes: [hi/lo][Kc][N_pad rows][128 B]
   long scale_off;    // ints: output exponent shift - E_out(n(r)), r < RB
   int R_full, C, r0, RB, R16, N_pad, Kc, basis;
-  double kin, kout, w;
+  int etab_off;      // exponents E_in[n], E_out[n] of the class's (component, level)
 };
 
 // Scaled, split, swizzled FP16 copy of an operator sub-block (one CTA each).
 __global__ void __launch_bounds__(256) k_tc_prep_ops(const TcOpJob* __restrict__ jobs, const cplx* __restrict__ ops,
-                                                     unsigned char* __restrict__ dst, int* __restrict__ rexp) {
+                                                     unsigned char* __restrict__ dst, int* __restrict__ rexp,
+                                                     const int* __restrict__ etab) {
   const TcOpJob jb = jobs[blockIdx.x];
   __shared__ int Eout[128];
   __shared__ int Ein[FMM_MAXP * FMM_MAXP + 2 * FMM_MAXP + 1];
   __shared__ double red[8];
-  for (int r = threadIdx.x; r < jb.RB; r += blockDim.x) Eout[r] = deg_exp(jb.kout, jb.w, deg_of(jb.basis, jb.r0 + r));
-  for (int c = threadIdx.x; c < jb.C; c += blockDim.x) Ein[c] = deg_exp(jb.kin, jb.w, deg_of(jb.basis, c));
+  const int* Et = etab + jb.etab_off;           // [E_in(0..MAXP) | E_out(0..MAXP)]
+  for (int r = threadIdx.x; r < jb.RB; r += blockDim.x) Eout[r] = Et[FMM_MAXP + 1 + deg_of(jb.basis, jb.r0 + r)];
+  for (int c = threadIdx.x; c < jb.C; c += blockDim.x) Ein[c] = Et[deg_of(jb.basis, c)];
   __syncthreads();
   const cplx* A = ops + jb.src_off;
   double mx = 0.0;
@@ -263,12 +284,16 @@ struct TcPart {
   int C, in_off, Kc, basis;
 };
 
-// Column of sorted pair k, scaled and split into the A tiles of each part of its run.
+// Column of sorted pair k, scaled and split into the A tiles of each part of
+// its run.  FP64 appears only in the loads: the degree and column scales are
+// applied to the exponent bits while rounding to FP32, and the rotation and
+// the symmetric-basis combination (reaction) run in FP32.
 __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __restrict__ perm,
                                                   const int* __restrict__ owner, const int* __restrict__ vidx,
                                                   BoxGeom B, OpIndex OI, const cplx* __restrict__ M,
                                                   const int* __restrict__ run_start, int nruns,
                                                   const int* __restrict__ run_part, const TcPart* __restrict__ parts,
+                                                  const int* __restrict__ etab, const float2* __restrict__ phase_f,
                                                   unsigned char* __restrict__ Abuf, int* __restrict__ isig) {
   const int P = (p + 1) * (p + 1);
   long k = blockIdx.x;
@@ -287,64 +312,65 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
   int T = owner[e], S = vidx[e];
   int comp = B.comp[T], lev = B.lev[T];
   const CompGeom& cg = OI.cgs[comp];
-  extern __shared__ cplx ys[];                 // [2 P]: rotated column, then its symmetric-basis form
-  __shared__ double red[2];
-  __shared__ double pw[FMM_MAXP + 1];          // 2^{-E_in(n)} of this box size and wave number
-  __shared__ double sc[(FMM_MAXP + 1) * (FMM_MAXP + 1)];   // per contraction entry of the current part
-  cplx* xs = ys + P;
+  extern __shared__ float2 xf[];              // [2 P]: scaled column, then its rotated symmetric form
+  __shared__ int red[2];
+  __shared__ int Ein[FMM_MAXP + 1];
+  float2* yf = xf + P;
   const cplx* Ms = M + (long)S * P;
-  if (cg.kind == CK_FREE) {
-    for (int i = threadIdx.x; i < P; i += blockDim.x) ys[i] = Ms[i];
-  } else {
+  const int* Et = etab + ((long)comp * 23 + lev) * 2 * (FMM_MAXP + 1);
+  for (int n = threadIdx.x; n <= p; n += blockDim.x) Ein[n] = Et[n];
+  __syncthreads();
+  // column exponent: largest binary exponent of the degree-scaled entries
+  int emax = -1 << 20;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    cplx x = Ms[i];
+    int en = Ein[deg_of(0, i)];
+    if (x.x != 0.0) emax = max(emax, dexp_of(x.x) - en);
+    if (x.y != 0.0) emax = max(emax, dexp_of(x.y) - en);
+  }
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  emax = max(red[0], red[1]);
+  const int ek = (emax > -(1 << 19)) ? emax + 1 : 0;      // entries below 1 after the column scale
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    cplx x = Ms[i];
+    int sh = -Ein[deg_of(0, i)] - ek;
+    xf[i] = make_float2(d2f_scaled(x.x, sh), d2f_scaled(x.y, sh));
+  }
+  __syncthreads();
+  const float2* src = xf;
+  if (cg.kind != CK_FREE) {
     const int* ct = B.coord + 3 * T;
     const int* cs = B.coord + 3 * S;
-    const cplx* ph = OI.phase + ((ct[1] - cs[1] + 3) * 7 + (ct[0] - cs[0] + 3)) * (2 * p + 1) + p;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-      int n = deg_of(0, i), mm = i - n * n - n;
-      xs[i] = cmul(Ms[i], ph[mm]);
-    }
-    __syncthreads();
+    const float2* ph = phase_f + ((ct[1] - cs[1] + 3) * 7 + (ct[0] - cs[0] + 3)) * (2 * p + 1) + p;
     const int np = (p + 1) * (p + 2) / 2;
-    const double rr = 0.70710678118654752440;
+    const float rr = 0.70710678118654752440f;
     for (int a = threadIdx.x; a < P; a += blockDim.x) {
       bool plus = a < np;
       int n = deg_of(plus ? 1 : 2, plus ? a : a - np);
       int mm = plus ? a - n * (n + 1) / 2 : a - np - n * (n - 1) / 2 + 1;
-      cplx u;
+      float2 u;
+      float2 x0 = xf[n * n + n + mm], p0 = ph[mm];
+      float2 r0 = make_float2(x0.x * p0.x - x0.y * p0.y, x0.x * p0.y + x0.y * p0.x);
       if (mm == 0) {
-        u = xs[n * n + n];
+        u = r0;
       } else {
-        double s = (mm & 1) ? -1.0 : 1.0;
-        cplx x0 = xs[n * n + n + mm], x1 = cscale(xs[n * n + n - mm], s);
-        u = cscale(plus ? cadd(x0, x1) : csub(x0, x1), rr);
+        float2 x1 = xf[n * n + n - mm], p1 = ph[-mm];
+        float s = (mm & 1) ? -1.0f : 1.0f;
+        float2 r1 = make_float2(s * (x1.x * p1.x - x1.y * p1.y), s * (x1.x * p1.y + x1.y * p1.x));
+        u = plus ? make_float2((r0.x + r1.x) * rr, (r0.y + r1.y) * rr)
+                 : make_float2((r0.x - r1.x) * rr, (r0.y - r1.y) * rr);
       }
-      ys[a] = u;
+      yf[a] = u;
     }
+    __syncthreads();
+    src = yf;
   }
-  const double w = cg.h2 / (double)(1 << lev);
-  for (int n = threadIdx.x; n <= p; n += blockDim.x) pw[n] = ldexp(1.0, -deg_exp(cg.ks, w, n));
-  __syncthreads();
   for (int q = 0; q < 2; ++q) {
     int pi = run_part[2 * run + q];
     if (pi < 0) continue;
     const TcPart pt = parts[pi];
-    double mx = 0.0;
-    for (int c = threadIdx.x; c < pt.C; c += blockDim.x) {
-      double f = pw[deg_of(pt.basis, c)];
-      sc[c] = f;
-      cplx v = ys[pt.in_off + c];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)) * f);
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    mx = fmax(red[0], red[1]);
-    int ek = 0;
-    if (mx > 0.0) frexp(mx, &ek);             // scaled entries below 1
-    const double sk = ldexp(1.0, -ek);
-    for (int c = threadIdx.x; c < pt.C; c += blockDim.x) sc[c] *= sk;
-    __syncthreads();
     const int units = pt.Kc * (kChunk / 8);
     const long tile_bytes = 2L * pt.Kc * kTileM * kRowBytes, half_bytes = (long)pt.Kc * kTileM * kRowBytes;
     const int tile = m / kTileM, row = m % kTileM;
@@ -358,9 +384,8 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
         float v = 0.0f;
         if (ji < 2 * pt.C) {
           bool re = ji < pt.C;
-          int c = re ? ji : ji - pt.C;
-          cplx y = ys[pt.in_off + c];
-          v = (float)((re ? y.x : y.y) * sc[c]);   // power-of-two scale: exact before the rounding to FP32
+          float2 y = src[pt.in_off + (re ? ji : ji - pt.C)];
+          v = re ? y.x : y.y;
         }
         split_half_f(v, hv[t], lv[t]);
       }
@@ -380,8 +405,12 @@ __global__ void __launch_bounds__(64) k_tc_gather(long nv, int p, const int* __r
       }
       for (int f = threadIdx.x; f < pad; f += blockDim.x) isig[pt.sig_off + m + 1 + f] = 0;
     }
-    __syncthreads();
   }
+}
+
+__global__ void k_tc_phase_f32(int n, const cplx* __restrict__ ph, float2* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)ph[i].x, (float)ph[i].y);
 }
 
 // One tile of 128 pairs times one operator sub-block.
@@ -513,6 +542,17 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
 }
 
 // ---------------------------------------------------------------- host driver
+// floor(log2 s_n), s_n = (k rho)^n / (2n+1)!!, rho = (sqrt 3 / 2) w: the
+// degree scale of the coefficients of a box of width w (see the header).
+static int deg_exp(double k, double w, int n) {
+  double x = k * 0.86602540378443864676 * w;
+  double s = 1.0;
+  for (int j = 1; j <= n; ++j) s *= x / (2.0 * j + 1.0);
+  int e;
+  frexp(s, &e);
+  return e - 1;
+}
+
 void launch_tc_run_info(int nruns, const int* rs, const int* perm, const int* owner, BoxGeom B, int* info,
                         cudaStream_t st);
 
@@ -538,6 +578,27 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   std::vector<int> info(2 * (size_t)nruns);
   FMM_CHECK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * 2 * (size_t)nruns, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
+  // degree-scale exponents of every (component, level): [E_in | E_out], shared
+  // by the operator conversion and the gather so that both use the same ones
+  const int nc = (int)cgh.size();
+  std::vector<int> et((size_t)nc * 23 * 2 * (FMM_MAXP + 1), 0);
+  for (int c = 0; c < nc; ++c)
+    for (int l = 0; l < 23; ++l) {
+      const double wl = cgh[c].h2 / (double)(1 << l);
+      int* E = et.data() + ((size_t)c * 23 + l) * 2 * (FMM_MAXP + 1);
+      for (int n = 0; n <= p; ++n) {
+        E[n] = deg_exp(cgh[c].ks, wl, n);
+        E[FMM_MAXP + 1 + n] = deg_exp(cgh[c].kt, wl, n);
+      }
+    }
+  int* d_et = (int*)tc_need(ws.tc_etab, sizeof(int) * et.size() + 64);
+  FMM_CHECK(cudaMemcpyAsync(d_et, et.data(), sizeof(int) * et.size(), cudaMemcpyHostToDevice, st));
+  const int nph = 49 * (2 * p + 1);
+  if (!tc.phase_ready) {
+    tc.phase_f.ensure(sizeof(float2) * nph);
+    LAUNCH(k_tc_phase_f32<<<(nph + 127) / 128, 128, 0, st>>>(nph, OI.phase, tc.phase_f.as<float2>()));
+    tc.phase_ready = true;
+  }
 
   std::vector<TcPart> parts;
   std::vector<int> run_part(2 * (size_t)nruns, -1);
@@ -551,8 +612,6 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
     const bool reac = hk[r] & 1;
     const int K = hc[r];
     const int comp = info[2 * r], lev = info[2 * r + 1];
-    const CompGeom& cg = cgh[comp];
-    const double w = cg.h2 / (double)(1 << lev);
     PartDesc pd[2];
     int npd = 0;
     if (!reac) pd[npd++] = {off, P, P, 0, 0, false};
@@ -603,9 +662,7 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
           jb.N_pad = ref.N_pad;
           jb.Kc = pt.Kc;
           jb.basis = d.basis;
-          jb.kin = cg.ks;
-          jb.kout = cg.kt;
-          jb.w = w;
+          jb.etab_off = (comp * 23 + lev) * 2 * (FMM_MAXP + 1);
           jobs.push_back(jb);
           tc.ops[key] = ref;
           tc.pending_reac.push_back(d.reac);
@@ -648,10 +705,10 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
     FMM_CHECK(cudaMemcpyAsync(dj, all.data(), sizeof(TcOpJob) * all.size(), cudaMemcpyHostToDevice, st));
     if (!jf.empty())
       LAUNCH(k_tc_prep_ops<<<(unsigned)jf.size(), 256, 0, st>>>(dj, free_ops, tc.bbuf.as<unsigned char>(),
-                                                               tc.sbuf.as<int>()));
+                                                               tc.sbuf.as<int>(), d_et));
     if (!jr.empty())
       LAUNCH(k_tc_prep_ops<<<(unsigned)jr.size(), 256, 0, st>>>(dj + jf.size(), reac_ops,
-                                                               tc.bbuf.as<unsigned char>(), tc.sbuf.as<int>()));
+                                                               tc.bbuf.as<unsigned char>(), tc.sbuf.as<int>(), d_et));
     FMM_CHECK(cudaGetLastError());
     tc.b_used_done = tc.b_used;
     tc.s_done = tc.s_used;
@@ -663,8 +720,9 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   TcPart* dparts = (TcPart*)tc_need(ws.tc_parts, sizeof(TcPart) * parts.size() + 64);
   FMM_CHECK(cudaMemcpyAsync(dparts, parts.data(), sizeof(TcPart) * parts.size(), cudaMemcpyHostToDevice, st));
   FMM_CHECK(cudaMemcpyAsync(d_part, run_part.data(), sizeof(int) * run_part.size(), cudaMemcpyHostToDevice, st));
-  LAUNCH(k_tc_gather<<<(unsigned)nv, 64, sizeof(cplx) * 2 * P, st>>>(nv, p, perm, owner, vidx, B, OI, M, d_rs, nruns,
-                                                                     d_part, dparts, Abuf, isig));
+  LAUNCH(k_tc_gather<<<(unsigned)nv, 64, sizeof(float2) * 2 * P, st>>>(nv, p, perm, owner, vidx, B, OI, M, d_rs,
+                                                                       nruns, d_part, dparts, d_et,
+                                                                       tc.phase_f.as<float2>(), Abuf, isig));
   // products
   TcItem* ditems = (TcItem*)tc_need(ws.tc_items, sizeof(TcItem) * items.size() + 64);
   FMM_CHECK(cudaMemcpyAsync(ditems, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice, st));

@@ -61,6 +61,12 @@ __device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coe
 // One CTA (128 threads) per target leaf: thread pairs (t, t + 64) share a
 // target and take alternate sources; the two halves are added at the end in
 // a fixed order.
+// F32 (mixed-precision form, free-space pairs only): positions relative to
+// the leaf's first target (one FP64 subtraction per point, exact enough that
+// r keeps ~1e-7 relative accuracy at the near-field distances), the kernel
+// e^{ikr}/(4 pi r) in FP32, and a compensated (Kahan) FP32 sum per target
+// that is added to the FP64 accumulator once per target.
+template <bool F32>
 __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearComp* __restrict__ ncs,
                        RuleView R, const double* __restrict__ spos, const cplx* __restrict__ sq,
                        const double* __restrict__ tpos, cplx* __restrict__ phi,
@@ -71,6 +77,13 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
   __shared__ double sx[NEAR_CHUNK], sy[NEAR_CHUNK], sz[NEAR_CHUNK];
   __shared__ cplx sqs[NEAR_CHUNK];
   __shared__ cplx half1[64];
+  __shared__ float fx[F32 ? NEAR_CHUNK : 1], fy[F32 ? NEAR_CHUNK : 1], fz[F32 ? NEAR_CHUNK : 1];
+  __shared__ float2 fq[F32 ? NEAR_CHUNK : 1];
+  const bool f32 = F32 && nc.kind == CK_FREE;
+  double ox = 0, oy = 0, oz = 0;               // anchor of the relative positions
+  if (f32) { ox = tpos[3 * B.tb[T]]; oy = tpos[3 * B.tb[T] + 1]; oz = tpos[3 * B.tb[T] + 2]; }
+  const float kf = (float)nc.k;
+  const float inv4pif = (float)(1.0 / (4.0 * FMM_PI));
   const cplx* coef = R.coef + nc.coef_off;
   const cplx* kzl = R.kz + (long)nc.l * R.Q;
   const cplx* kzp = R.kz + (long)nc.lp * R.Q;
@@ -83,6 +96,8 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
     double x = 0, y = 0, z = 0;
     if (act) { x = tpos[3 * t]; y = tpos[3 * t + 1]; z = tpos[3 * t + 2]; }
     cplx acc = C(0, 0);
+    const float xr = (float)(x - ox), yr = (float)(y - oy), zr = (float)(z - oz);
+    float ar = 0.f, cr = 0.f, ai = 0.f, ci = 0.f;    // compensated FP32 sums
     // list walk: U(T), W(T), then X(A) for A = T and its ancestors
     int A = T;
     int phase = 0;   // 0: U, 1: W, 2: X of A
@@ -106,10 +121,31 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
         for (int kk = threadIdx.x; kk < ns; kk += blockDim.x) {
           sx[kk] = spos[3 * (s0 + kk)]; sy[kk] = spos[3 * (s0 + kk) + 1]; sz[kk] = spos[3 * (s0 + kk) + 2];
           sqs[kk] = sq[s0 + kk];
+          if (F32 && f32) {
+            fx[kk] = (float)(sx[kk] - ox); fy[kk] = (float)(sy[kk] - oy); fz[kk] = (float)(sz[kk] - oz);
+            fq[kk] = make_float2((float)sqs[kk].x, (float)sqs[kk].y);
+          }
         }
         __syncthreads();
         if (act) {
-          if (nc.kind == CK_FREE) {
+          if (F32 && f32) {
+            for (int kk = par; kk < ns; kk += 2) {
+              float dx = xr - fx[kk], dy = yr - fy[kk], dz = zr - fz[kk];
+              if (dx == 0.f && dy == 0.f && dz == 0.f && x == sx[kk] && y == sy[kk] && z == sz[kk]) continue;
+              float r2 = dx * dx + dy * dy + dz * dz;
+              float rinv = rsqrtf(r2);
+              float sn, cs;
+              sincosf(kf * (r2 * rinv), &sn, &cs);
+              float f = rinv * inv4pif;
+              float2 qv = fq[kk];
+              float tr = f * (cs * qv.x - sn * qv.y), ti = f * (cs * qv.y + sn * qv.x);
+              float yv = tr - cr, tt = ar + yv;
+              cr = (tt - ar) - yv; ar = tt;
+              yv = ti - ci; tt = ai + yv;
+              ci = (tt - ai) - yv; ai = tt;
+              ++my_pairs;
+            }
+          } else if (nc.kind == CK_FREE) {
             for (int kk = par; kk < ns; kk += 2) {
               double dx = x - sx[kk], dy = y - sy[kk], dz = z - sz[kk];
               if (dx == 0.0 && dy == 0.0 && dz == 0.0) continue;   // bitwise-identical points (j = i)
@@ -137,6 +173,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
         }
       }
     }
+    if (F32 && f32) acc = cadd(acc, C((double)ar - (double)cr, (double)ai - (double)ci));
     __syncthreads();
     if (par == 1) half1[lane_t] = acc;
     __syncthreads();
@@ -270,8 +307,11 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
-                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st) {
-  if (n) LAUNCH(k_near<<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
+                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st,
+                 bool f32) {
+  if (!n) return;
+  if (f32) LAUNCH(k_near<true><<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
+  else LAUNCH(k_near<false><<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
 }
 
 // Dependent FP64 FMA chains (8 independent chains per thread).
