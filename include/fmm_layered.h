@@ -56,6 +56,11 @@ extern "C" {
                                  reaction near field and all sums over
                                  translations stay FP64.  Relative error of
                                  the potentials below 1e-5.                    */
+#define FMM_SURROGATE    4u   /* once fmm_layered_surrogate_train has run: the
+                                 reaction components of the near field and of
+                                 fmm_layered_direct come from the learned
+                                 surrogate wherever its held-out check passed
+                                 (quadrature elsewhere)                        */
 
 typedef struct fmm_layered fmm_layered_t;
 
@@ -106,7 +111,7 @@ typedef struct {
  *               condition [eps du/dz] = 0 (host; NULL means all 1)
  *   p           expansion order, 1 <= p <= 16 (terms n = 0..p)
  *   leaf        maximum number of sources or targets in a leaf box, >= 1
- *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER | FMM_MIXED
+ *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER | FMM_MIXED | FMM_SURROGATE
  *   out         receives the handle (NULL on failure)
  * Builds the contour quadrature rule and the reaction densities sigma at its
  * nodes on the current device.  Returns FMM_ERR_ARG for invalid input.
@@ -160,6 +165,36 @@ int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const long* n_src,
                              const double* const* src_xyz, const double* const* charges,
                              const long* n_tgt, const double* const* tgt_xyz,
                              double* const* out, void* stream);
+
+/*
+ * Learned surrogate of the reaction components (the form that replaces the
+ * Sommerfeld quadrature of eq. generalcomponentsimag in the near field).
+ * For every reaction component (l, l', a, b) of the medium, draws
+ * samples_per_component points uniformly in the box rho in [0, rho_max],
+ * zt, zs in [z_min, z_max] (zt: target distance to the component's reference
+ * interface, zs: image depth) plus 1/8 as many held-out points (seeded
+ * counter-based generator), evaluates the component there with the
+ * library's quadrature, and trains one MLP 3 -> 64 -> 64 -> 64 -> 2 (GELU;
+ * BF16 weights and layer inputs, FP32 accumulation; Adam on FP32 master
+ * weights; minibatch 1024, cosine learning-rate decay) for `steps` steps on
+ * y = 4 pi R u, R = sqrt(rho^2 + (zt + zs)^2).  The held-out relative RMS
+ * error is then measured on each cell of a 4 x 4 x 4 grid over the box; the
+ * surrogate is used (with FMM_SURROGATE) only in cells within `bound`, and
+ * the quadrature everywhere else and outside the box.  Retraining replaces the
+ * previous networks.  Runs on `stream` and returns when done.
+ * FMM_ERR_ARG for a single layer or invalid box/sizes.
+ */
+int fmm_layered_surrogate_train(fmm_layered_t* h, double rho_max, double z_min,
+                                double z_max, long samples_per_component,
+                                int steps, double bound, unsigned long long seed,
+                                void* stream);
+
+/* Held-out verdict of the last training: cell_err[slot * 64 + cell] (relative
+ * RMS error, -1 where not judged) and cell_ok (1 where used), slot =
+ * ((l (L+1) + l') 2 + a) 2 + b, cell = (c_rho 4 + c_zt) 4 + c_zs; arrays of
+ * 4 (L+1)^2 64 entries (host, either may be NULL).  FMM_ERR_ARG if untrained. */
+int fmm_layered_surrogate_report(const fmm_layered_t* h, double* cell_err,
+                                 unsigned char* cell_ok);
 
 /* Same as fmm_layered_eval with HOST buffers: copies inputs to the device,
  * evaluates and copies the potentials back (all on `stream`). */

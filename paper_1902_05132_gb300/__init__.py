@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libfmmlayered.so")
 FMM_PLAIN_FP64 = 0
 FMM_NORM_PAPER = 1
 FMM_MIXED = 2
+FMM_SURROGATE = 4
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "point on an interface", -3: "non-finite input",
           -4: "CUDA error", -5: "out of device memory", -6: "timeout", -7: "unsupported"}
@@ -51,7 +52,8 @@ class Stats(ctypes.Structure):
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
             "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
             "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
-            "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched"]
+            "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched",
+            "fmm_layered_surrogate_train", "fmm_layered_surrogate_report"]
 
 _lib = None
 
@@ -78,6 +80,11 @@ def lib():
         f.restype = i
     L.fmm_layered_eval_batched.argtypes = [i, d, d, d, d, d, d, d, v]
     L.fmm_layered_eval_batched.restype = i
+    L.fmm_layered_surrogate_train.argtypes = [v, ctypes.c_double, ctypes.c_double, ctypes.c_double, l, i,
+                                              ctypes.c_double, ctypes.c_ulonglong, v]
+    L.fmm_layered_surrogate_train.restype = i
+    L.fmm_layered_surrogate_report.argtypes = [v, d, d]
+    L.fmm_layered_surrogate_report.restype = i
     L.fmm_layered_stats.argtypes = [v, ctypes.POINTER(Stats)]
     L.fmm_layered_stats.restype = i
     L.fmm_layered_num_components.argtypes = [v]
@@ -140,7 +147,7 @@ class LayeredFMM:
     mixed=True runs the M2L translations on the tensor cores (FP16 hi/lo
     operands, FP32 accumulation); every other stage stays FP64."""
 
-    def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False, mixed=False):
+    def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False, mixed=False, surrogate=False):
         L = lib()
         self.k = np.ascontiguousarray(k, dtype=np.float64)
         self.d = np.ascontiguousarray(d, dtype=np.float64)
@@ -149,7 +156,8 @@ class LayeredFMM:
         h = ctypes.c_void_p()
         rc = L.fmm_layered_create(len(self.k), _ptr(self.k), _ptr(self.d) if len(self.d) else None,
                                   _ptr(self.eps), self.p, self.leaf,
-                                  (FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64) | (FMM_MIXED if mixed else 0),
+                                  (FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64) | (FMM_MIXED if mixed else 0)
+                                  | (FMM_SURROGATE if surrogate else 0),
                                   ctypes.byref(h))
         if rc != 0:
             raise FmmError(rc, L.fmm_layered_last_error(None).decode())
@@ -214,6 +222,23 @@ class LayeredFMM:
         self._check(lib().fmm_layered_eval_host(self.h, len(src), _ptr(src), _ptr(qr), len(tgt), _ptr(tgt),
                                                 _ptr(out), st))
         return out.view(np.complex128)
+
+    def train_surrogate(self, rho_max, z_min, z_max, samples=16384, steps=2000, bound=1e-5, seed=0, stream=None):
+        """Train the learned surrogate of the reaction components
+        (fmm_layered_surrogate_train); returns the per-cell report."""
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(lib().fmm_layered_surrogate_train(self.h, float(rho_max), float(z_min), float(z_max),
+                                                      int(samples), int(steps), float(bound),
+                                                      ctypes.c_ulonglong(seed), st))
+        return self.surrogate_report()
+
+    def surrogate_report(self):
+        """(cell_err, cell_ok), shape [4 L1^2, 64]; slot ((l*L1 + l')*2 + a)*2 + b."""
+        n = 4 * len(self.k) ** 2 * 64
+        err = np.zeros(n, dtype=np.float64)
+        ok = np.zeros(n, dtype=np.uint8)
+        self._check(lib().fmm_layered_surrogate_report(self.h, _ptr(err), _ptr(ok)))
+        return err.reshape(-1, 64), ok.reshape(-1, 64).astype(bool)
 
     def stats(self):
         s = Stats()

@@ -69,6 +69,7 @@ static T* upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 
 // ---------------------------------------------------------------- create
 void init_legendre_tables();
+SurrView surrogate_view(const fmm_layered* h);
 
 static void create_impl(fmm_layered* h) {
   FMM_CHECK(cudaGetDevice(&h->dev));
@@ -151,6 +152,7 @@ extern "C" int fmm_layered_create(int n_layers, const double* k, const double* i
 
 extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   if (!h) return;
+  h->surr.release();
   if (h->bstream) cudaStreamDestroy(h->bstream);
   if (h->bdone) cudaEventDestroy(h->bdone);
   DevBuf* all[] = {&h->d_k, &h->d_d, &h->d_eps, &h->rule.kr, &h->rule.w, &h->rule.kz, &h->rule.sigma,
@@ -226,7 +228,9 @@ extern "C" int fmm_layered_direct(fmm_layered_t* h, long ns, const double* src, 
       }
     if (h->L1 > 1 && std::isfinite(gmin + smin)) rule_extend(h, h->rule.ta + 30.0 / (gmin + smin), st);
     cplx* coef = rule_coef(h, st);
-    launch_direct(nt, tgt, ns, src, q, medium_of(h), make_rule_view(h->rule, coef), coef, out, st);
+    RuleView rv = make_rule_view(h->rule, coef);
+    rv.surr = surrogate_view(h);
+    launch_direct(nt, tgt, ns, src, q, medium_of(h), rv, coef, out, st);
     if (h->flags & FMM_NORM_PAPER) launch_norm_paper(nt, tgt, medium_of(h), out, st);
     FMM_CHECK(cudaGetLastError());
     FMM_CHECK(cudaStreamSynchronize(st));
@@ -608,7 +612,9 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st,
               (h->flags & FMM_MIXED) != 0);
   E.mark(6, st);
-  launch_near(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, make_rule_view(h->rule, coef),
+  RuleView rv_reac = make_rule_view(h->rule, coef);
+  rv_reac.surr = surrogate_view(h);
+  launch_near(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, rv_reac,
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 2, st, false);
   FMM_CHECK(cudaGetLastError());
   E.mark(7, st);

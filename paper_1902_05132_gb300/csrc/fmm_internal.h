@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fmm_math.cuh"
+#include "surrogate.cuh"
 #include "../../include/fmm_layered.h"
 
 #define FMM_CHECK(call)                                                    \
@@ -149,6 +150,20 @@ struct TcCache {
   std::vector<bool> pending_reac;
 };
 
+// Learned surrogate of the reaction components: training data, networks and
+// the per-cell verdict of the held-out check.
+struct SurrState {
+  bool trained = false;
+  double rho_max = 0, z_min = 0, z_max = 0, bound = 0;
+  DevBuf coef, slots, X, Y, Xh, Yh, wf, m, v, w16, gpart, acc, ok;
+  std::vector<double> cell_err;           // [slot][64] held-out relative RMS error, -1 if not judged
+  std::vector<unsigned char> cell_ok;     // [slot][64] within the bound
+  void release() {
+    DevBuf* all[] = {&coef, &slots, &X, &Y, &Xh, &Yh, &wf, &m, &v, &w16, &gpart, &acc, &ok};
+    for (DevBuf* b : all) b->release();
+  }
+};
+
 struct fmm_layered {
   int L1 = 0;               // number of layers
   std::vector<double> k, d, eps;
@@ -161,6 +176,7 @@ struct fmm_layered {
   Workspace ws;
   OpCache cache;
   TcCache tc;
+  SurrState surr;
   fmm_stats_t stats{};
   std::string err;
   // state of the last evaluation (for export)
@@ -214,6 +230,7 @@ struct RuleView {
   const cplx* kz;          // [L1][Q]
   int Q, n_near, per_panel, n_panels;
   double ta, panel;
+  SurrView surr;           // learned surrogate of the reaction components (w == nullptr: none)
 };
 struct NearComp { int kind, l, lp, a, b; double k; double dref; long coef_off; };
 struct NearBoxes { const int *comp, *lev, *sb, *se, *tb, *te, *parent; const int *uo, *ui, *wo, *wi, *xo, *xi; };

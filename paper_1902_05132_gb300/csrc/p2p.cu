@@ -53,6 +53,26 @@ __device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coe
   return cadd(acc, C(tail, 0.0));
 }
 
+// Reaction component `slot` of one pair: the learned surrogate where it is
+// trained and its held-out check passed for the cell of (rho, zt, zs), the
+// quadrature everywhere else.
+__device__ inline cplx reac_value(const RuleView& R, int slot, const cplx* __restrict__ coef,
+                                  const cplx* __restrict__ kzl, const cplx* __restrict__ kzp, double rho, double zt,
+                                  double zs, int* nq_out = nullptr) {
+  if (R.surr.w) {
+    float x[3];
+    int cell;
+    if (surr_inputs(R.surr, rho, zt, zs, x, &cell) && R.surr.ok[slot * SURR_CELLS + cell]) {
+      float2 y = surr_forward(R.surr.w + (long)slot * SURR_NPAR, x);
+      double h = zt + zs;
+      double f = 1.0 / (4.0 * FMM_PI * sqrt(rho * rho + h * h));
+      if (nq_out) *nq_out = 0;
+      return C((double)y.x * f, (double)y.y * f);
+    }
+  }
+  return reac_pair(R, coef, kzl, kzp, rho, zt, zs, nq_out);
+}
+
 
 
 
@@ -165,7 +185,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
               double rho = sqrt(dx * dx + dy * dy);
               double zs = fabs(sz[kk] - nc.dref);
               int nq;
-              cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs, &nq), sqs[kk]);
+              cfma(acc, reac_value(R, (int)(nc.coef_off / R.Q), coef, kzl, kzp, rho, zt, zs, &nq), sqs[kk]);
               ++my_pairs;
               my_nodes += nq;
             }
@@ -237,8 +257,9 @@ __global__ void k_direct(long nt, const double* __restrict__ tgt, long ns, const
         for (int b = 0; b < 2; ++b) {
           if (b == AR_UP ? !(ls < md.L1 - 1) : !(ls > 0)) continue;
           double zs = (b == AR_UP) ? (sz[k] - md.d[ls]) : (md.d[ls - 1] - sz[k]);
-          const cplx* coef = coef_all + ((((long)lt * md.L1 + ls) * 2 + a) * 2 + b) * R.Q;
-          cfma(acc, reac_pair(R, coef, kzl, kzp, rho, zt, zs), sqs[k]);
+          const int slot = ((lt * md.L1 + ls) * 2 + a) * 2 + b;
+          const cplx* coef = coef_all + (long)slot * R.Q;
+          cfma(acc, reac_value(R, slot, coef, kzl, kzp, rho, zt, zs), sqs[k]);
         }
       }
     }
@@ -303,7 +324,33 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
   v.n_panels = R.n_tail_panels;
   v.ta = R.ta;
   v.panel = R.panel;
+  v.surr = SurrView{};
   return v;
+}
+
+// Training and held-out samples of the surrogate: points drawn uniformly in
+// the box by a counter-based generator, component values by the quadrature.
+__global__ void k_surr_samples(long n, long nper, const int* __restrict__ slots, int L1, SurrView box,
+                               RuleView R, unsigned long long seed, float* __restrict__ X, float* __restrict__ Y) {
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int slot = slots[e / nper];
+  const int lp = (slot >> 2) % L1, l = (slot >> 2) / L1;      // slot = ((l L1 + l') 2 + a) 2 + b
+  double u0 = surr_uniform(seed, 3 * e), u1 = surr_uniform(seed, 3 * e + 1), u2 = surr_uniform(seed, 3 * e + 2);
+  double rho = u0 * box.rho_max;
+  double zt = box.z_min + u1 * (box.z_max - box.z_min), zs = box.z_min + u2 * (box.z_max - box.z_min);
+  cplx u = reac_pair(R, R.coef + (long)slot * R.Q, R.kz + (long)l * R.Q, R.kz + (long)lp * R.Q, rho, zt, zs);
+  double f = 4.0 * FMM_PI * sqrt(rho * rho + (zt + zs) * (zt + zs));
+  X[3 * e] = (float)(2.0 * u0 - 1.0);
+  X[3 * e + 1] = (float)(2.0 * u1 - 1.0);
+  X[3 * e + 2] = (float)(2.0 * u2 - 1.0);
+  Y[2 * e] = (float)(u.x * f);
+  Y[2 * e + 1] = (float)(u.y * f);
+}
+
+void launch_surr_samples(long n, long nper, const int* slots, int L1, SurrView box, RuleView R,
+                         unsigned long long seed, float* X, float* Y, cudaStream_t st) {
+  if (n) LAUNCH(k_surr_samples<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, nper, slots, L1, box, R, seed, X, Y));
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
