@@ -189,6 +189,10 @@ int fmm_layered_surrogate_train(fmm_layered_t* h, double rho_max, double z_min,
                                 int steps, double bound, unsigned long long seed,
                                 void* stream);
 
+/* Re-judge the cells of the last training against a new bound (no
+ * retraining; synchronous).  FMM_ERR_ARG if untrained or bound <= 0. */
+int fmm_layered_surrogate_set_bound(fmm_layered_t* h, double bound);
+
 /* Held-out verdict of the last training: cell_err[slot * 64 + cell] (relative
  * RMS error, -1 where not judged) and cell_ok (1 where used), slot =
  * ((l (L+1) + l') 2 + a) 2 + b, cell = (c_rho 4 + c_zt) 4 + c_zs; arrays of

@@ -53,7 +53,7 @@ EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error
             "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
             "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
             "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched",
-            "fmm_layered_surrogate_train", "fmm_layered_surrogate_report"]
+            "fmm_layered_surrogate_train", "fmm_layered_surrogate_report", "fmm_layered_surrogate_set_bound"]
 
 _lib = None
 
@@ -83,6 +83,8 @@ def lib():
     L.fmm_layered_surrogate_train.argtypes = [v, ctypes.c_double, ctypes.c_double, ctypes.c_double, l, i,
                                               ctypes.c_double, ctypes.c_ulonglong, v]
     L.fmm_layered_surrogate_train.restype = i
+    L.fmm_layered_surrogate_set_bound.argtypes = [v, ctypes.c_double]
+    L.fmm_layered_surrogate_set_bound.restype = i
     L.fmm_layered_surrogate_report.argtypes = [v, d, d]
     L.fmm_layered_surrogate_report.restype = i
     L.fmm_layered_stats.argtypes = [v, ctypes.POINTER(Stats)]
@@ -230,6 +232,11 @@ class LayeredFMM:
         self._check(lib().fmm_layered_surrogate_train(self.h, float(rho_max), float(z_min), float(z_max),
                                                       int(samples), int(steps), float(bound),
                                                       ctypes.c_ulonglong(seed), st))
+        return self.surrogate_report()
+
+    def surrogate_set_bound(self, bound):
+        """Use the surrogate only in cells whose held-out error is within `bound`."""
+        self._check(lib().fmm_layered_surrogate_set_bound(self.h, float(bound)))
         return self.surrogate_report()
 
     def surrogate_report(self):

@@ -342,6 +342,23 @@ extern "C" int fmm_layered_surrogate_train(fmm_layered_t* h, double rho_max, dou
   return FMM_OK;
 }
 
+extern "C" int fmm_layered_surrogate_set_bound(fmm_layered_t* h, double bound) {
+  if (!h) return FMM_ERR_ARG;
+  h->err.clear();
+  SurrState& S = h->surr;
+  if (!S.trained || !(bound > 0)) {
+    h->err = "no trained surrogate, or bound <= 0";
+    return FMM_ERR_ARG;
+  }
+  for (size_t i = 0; i < S.cell_err.size(); ++i) S.cell_ok[i] = (S.cell_err[i] >= 0.0 && S.cell_err[i] <= bound) ? 1 : 0;
+  if (cudaMemcpy(S.ok.ptr, S.cell_ok.data(), S.cell_ok.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    h->err = "copy of the cell verdicts failed";
+    return FMM_ERR_CUDA;
+  }
+  S.bound = bound;
+  return FMM_OK;
+}
+
 extern "C" int fmm_layered_surrogate_report(const fmm_layered_t* h, double* cell_err, unsigned char* cell_ok) {
   if (!h || !h->surr.trained) return FMM_ERR_ARG;
   const size_t n = h->surr.cell_err.size();

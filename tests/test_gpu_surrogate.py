@@ -67,3 +67,7 @@ def test_surrogate_loose_bound_error_within_bound():
     fa = plain.eval(src, q, tgt).cpu().numpy()
     fb = surr.eval(src, q, tgt).cpu().numpy()
     assert rel_l2(fb, fa) < bound
+    # re-judged against a bound no cell meets: the quadrature everywhere again
+    _, ok2 = surr.surrogate_set_bound(1e-9)
+    assert ok2.sum() == 0
+    assert np.array_equal(surr.direct(src, q, tgt).cpu().numpy(), a)
