@@ -286,11 +286,6 @@ static void gemm_tiles(int R, int& RB, int& CB) {
   RB = std::min(R, 96);
   CB = (int)(kGemmSmemCap / gemm_smem(RB, 1, full_tk(RB)));
 }
-static int R_blocks(int R) {
-  int RB, CB;
-  gemm_tiles(R, RB, CB);
-  return (R + RB - 1) / RB;
-}
 // Largest shared memory of any block of an R x R operator.
 static size_t gemm_smem_max(int R) {
   int RB, CB;
@@ -366,7 +361,7 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
                                                                    ws.g_Y.as<cplx>()));
     FMM_CHECK(cudaStreamSynchronize(st));
     // batches and tiles
-    std::vector<GemmBatch> bat;
+    std::vector<GemmBatch> bfree, breac;
     long k0 = 0;
     double macs = 0.0;       // complex multiply-adds of the translations (operator entries x columns)
     for (int r = 0; r < nruns; ++r) {
@@ -375,17 +370,24 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
       int K = hc[r];
       // one batch per operator block, split into chunks of at most 128
       // columns so that large classes spread over several CTAs
+      // free-space and reaction operators live in different buffers: the
+      // batch offsets index the buffer of their kind (free batches launch first)
+      std::vector<GemmBatch>& dst = reac ? breac : bfree;
       auto add = [&](long a_off, int R, long yz) {
         int RB, CB;
         gemm_tiles(R, RB, CB);
-        for (int r0 = 0; r0 < R; r0 += RB)
-          for (int c0 = 0; c0 < K; c0 += 128) {
+        for (int r0 = 0; r0 < R; r0 += RB) {
+          const int rb = std::min(RB, R - r0), tk = gemm_tk(rb, CB);
+          // column chunks of about 128, a whole number of column tiles (tk * Z_KB)
+          const int kt = tk * Z_KB, chunk = std::max(kt, (128 / kt) * kt);
+          for (int c0 = 0; c0 < K; c0 += chunk) {
             GemmBatch g{};
-            g.a_off = a_off; g.R = R; g.C = R; g.K = std::min(128, K - c0);
+            g.a_off = a_off; g.R = R; g.C = R; g.K = std::min(chunk, K - c0);
             g.y_off = (k0 + c0) * P + yz; g.z_off = (k0 + c0) * P + yz; g.ldy = P; g.ldz = P;
-            g.r0 = r0; g.RB = std::min(RB, R - r0); g.CB = CB; g.TK = gemm_tk(g.RB, CB);
-            bat.push_back(g);
+            g.r0 = r0; g.RB = rb; g.CB = CB; g.TK = tk;
+            dst.push_back(g);
           }
+        }
       };
       if (!reac) {
         add(off, P, 0);
@@ -397,20 +399,8 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
       }
       k0 += K;
     }
-    ws.g_bat.ensure(sizeof(GemmBatch) * bat.size() + 64);
+    ws.g_bat.ensure(sizeof(GemmBatch) * (bfree.size() + breac.size()) + 64);
     GemmBatch* dbat = ws.g_bat.as<GemmBatch>();
-    // free-space and reaction operators live in different buffers: the
-    // batch offsets index the buffer of their kind; order batches free first
-    std::vector<GemmBatch> bfree, breac;
-    {
-      size_t bi = 0;
-      for (int r = 0; r < nruns; ++r) {
-        bool reac = hk[r] & 1;
-        int nchunk = (hc[r] + 127) / 128;
-        int nb_rows = reac ? (R_blocks(np) + (nm ? R_blocks(nm) : 0)) : R_blocks(P);
-        for (int c = 0; c < nchunk * nb_rows; ++c) (reac ? breac : bfree).push_back(bat[bi++]);
-      }
-    }
     std::vector<GemmBatch> ordered = bfree;
     ordered.insert(ordered.end(), breac.begin(), breac.end());
     FMM_CHECK(cudaMemcpyAsync(dbat, ordered.data(), sizeof(GemmBatch) * ordered.size(), cudaMemcpyHostToDevice, st));
