@@ -65,59 +65,50 @@ __global__ void k_v_keys(long nv, const int* __restrict__ owner, const int* __re
 }
 
 // Y[k] = column of sorted pair k (P complex): M_S, or for reaction pairs the
-// rotated expansion in the symmetric basis [plus (np) | minus (nm)].
+// rotated expansion in the symmetric basis [plus (np) | minus (nm)].  One
+// thread per output coefficient (each reads at most two coefficients of M_S).
 __global__ void k_m2l_gather(long nv, int p, const int* __restrict__ perm, const int* __restrict__ owner,
                              const int* __restrict__ vidx, BoxGeom B, OpIndex OI, const cplx* __restrict__ M,
                              cplx* __restrict__ Y) {
   const int P = (p + 1) * (p + 1);
-  long k = blockIdx.x;
-  if (k >= nv) return;
-  int e = perm[k];
-  int T = owner[e], S = vidx[e];
-  int comp = B.comp[T];
-  const CompGeom& cg = OI.cgs[comp];
-  extern __shared__ cplx xs[];
+  const long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (g >= nv * P) return;
+  const long k = g / P;
+  const int a = (int)(g - k * P);
+  const int e = perm[k];
+  const int T = owner[e], S = vidx[e];
+  const CompGeom& cg = OI.cgs[B.comp[T]];
   const cplx* Ms = M + (long)S * P;
   if (cg.kind == CK_FREE) {
-    for (int i = threadIdx.x; i < P; i += blockDim.x) Y[k * P + i] = Ms[i];
+    Y[g] = Ms[a];
     return;
   }
   const int* ct = B.coord + 3 * T;
   const int* cs = B.coord + 3 * S;
   const cplx* ph = OI.phase + ((ct[1] - cs[1] + 3) * 7 + (ct[0] - cs[0] + 3)) * (2 * p + 1) + p;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    int n = (int)floor(sqrt((double)i));
-    while ((n + 1) * (n + 1) <= i) ++n;
-    while (n * n > i) --n;
-    int m = i - n * n - n;
-    xs[i] = cmul(Ms[i], ph[m]);
-  }
-  __syncthreads();
   const int np = (p + 1) * (p + 2) / 2;
-  const double r = 0.70710678118654752440;
-  for (int a = threadIdx.x; a < P; a += blockDim.x) {
-    int n, m;
-    bool plus = a < np;
-    if (plus) {
-      n = 0;
-      while ((n + 1) * (n + 2) / 2 <= a) ++n;
-      m = a - n * (n + 1) / 2;
-    } else {
-      int b = a - np;
-      n = 1;
-      while (n * (n + 1) / 2 <= b) ++n;
-      m = b - n * (n - 1) / 2 + 1;
-    }
-    cplx u;
-    if (m == 0) {
-      u = xs[n * n + n];
-    } else {
-      double s = (m & 1) ? -1.0 : 1.0;
-      cplx x0 = xs[n * n + n + m], x1 = cscale(xs[n * n + n - m], s);
-      u = cscale(plus ? cadd(x0, x1) : csub(x0, x1), r);
-    }
-    Y[k * P + a] = u;
+  const bool plus = a < np;
+  int n, m;
+  if (plus) {
+    n = 0;
+    while ((n + 1) * (n + 2) / 2 <= a) ++n;
+    m = a - n * (n + 1) / 2;
+  } else {
+    const int b = a - np;
+    n = 1;
+    while (n * (n + 1) / 2 <= b) ++n;
+    m = b - n * (n - 1) / 2 + 1;
   }
+  const cplx x0 = cmul(Ms[n * n + n + m], ph[m]);
+  cplx u;
+  if (m == 0) {
+    u = x0;
+  } else {
+    const double s = (m & 1) ? -1.0 : 1.0;
+    const cplx x1 = cscale(cmul(Ms[n * n + n - m], ph[-m]), s);
+    u = cscale(plus ? cadd(x0, x1) : csub(x0, x1), 0.70710678118654752440);
+  }
+  Y[g] = u;
 }
 
 // Batched complex GEMM: for every batch, Z[k][r] = sum_c A[c][r] Y[k][c]
@@ -199,8 +190,13 @@ __global__ void __launch_bounds__(128) k_zgemm_res(const GemmBatch* __restrict__
   }
 }
 
-// L_T = sum over V(T), in list order, of the translated columns (reaction:
-// back from the symmetric basis, then rotated back).  One CTA per target box.
+// L_T = sum over V(T) of the translated columns.  Free space: in list order.
+// Reaction: the way back from the symmetric basis and the rotation by
+// e^{-im phi} are linear and depend on the pair only through its horizontal
+// offset (phi), so the columns are first summed per offset (offsets in
+// increasing index, list order within one), and each offset's sum is
+// transformed once.  One CTA per target box; deterministic.
+#define REDUCE_MAXV 512
 __global__ void k_m2l_reduce(int p, const int* __restrict__ boxes, BoxGeom B, OpIndex OI,
                              const int* __restrict__ voff, const int* __restrict__ vidx,
                              const int* __restrict__ inv, const cplx* __restrict__ Z, cplx* __restrict__ L) {
@@ -211,6 +207,25 @@ __global__ void k_m2l_reduce(int p, const int* __restrict__ boxes, BoxGeom B, Op
   const int np = (p + 1) * (p + 2) / 2;
   const double r = 0.70710678118654752440;
   const int* ct = B.coord + 3 * T;
+  const int e0 = voff[T], nvl = voff[T + 1] - e0;
+  __shared__ int phi_of[REDUCE_MAXV], order[REDUCE_MAXV], start[50];
+  const bool grouped = reac && nvl <= REDUCE_MAXV;
+  if (grouped) {
+    for (int j = threadIdx.x; j < nvl; j += blockDim.x) {
+      const int* cs = B.coord + 3 * vidx[e0 + j];
+      phi_of[j] = (ct[1] - cs[1] + 3) * 7 + (ct[0] - cs[0] + 3);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {                     // stable counting sort by offset
+      for (int f = 0; f < 50; ++f) start[f] = 0;
+      for (int j = 0; j < nvl; ++j) ++start[phi_of[j] + 1];
+      for (int f = 0; f < 49; ++f) start[f + 1] += start[f];
+      int fill[49];
+      for (int f = 0; f < 49; ++f) fill[f] = start[f];
+      for (int j = 0; j < nvl; ++j) order[fill[phi_of[j]]++] = j;
+    }
+    __syncthreads();
+  }
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     int n = (int)floor(sqrt((double)i));
     while ((n + 1) * (n + 1) <= i) ++n;
@@ -219,11 +234,27 @@ __global__ void k_m2l_reduce(int p, const int* __restrict__ boxes, BoxGeom B, Op
     int ip = n * (n + 1) / 2 + am, im = am ? np + n * (n - 1) / 2 + am - 1 : 0;
     double sg = (m < 0 && (am & 1)) ? -1.0 : 1.0;
     cplx acc = C(0, 0);
-    for (int e = voff[T]; e < voff[T + 1]; ++e) {
-      const cplx* z = Z + (long)inv[e] * P;
-      if (!reac) {
-        acc = cadd(acc, z[i]);
-      } else {
+    if (!reac) {
+      for (int e = e0; e < e0 + nvl; ++e) acc = cadd(acc, Z[(long)inv[e] * P + i]);
+    } else if (grouped) {
+      for (int f = 0; f < 49; ++f) {
+        if (start[f + 1] == start[f]) continue;
+        cplx zp = C(0, 0), zm = C(0, 0);
+        for (int j = start[f]; j < start[f + 1]; ++j) {
+          const cplx* z = Z + (long)inv[e0 + order[j]] * P;
+          zp = cadd(zp, z[ip]);
+          if (m != 0) zm = cadd(zm, z[im]);
+        }
+        cplx v;
+        if (m == 0) v = zp;
+        else if (m > 0) v = cscale(cadd(zp, zm), r);
+        else v = cscale(csub(zp, zm), r * sg);
+        const cplx* ph = OI.phase + f * (2 * p + 1) + p;
+        acc = cadd(acc, cmul(v, cconj(ph[m])));
+      }
+    } else {
+      for (int e = e0; e < e0 + nvl; ++e) {
+        const cplx* z = Z + (long)inv[e] * P;
         cplx v;
         if (m == 0) v = z[ip];
         else if (m > 0) v = cscale(cadd(z[ip], z[im]), r);
@@ -357,8 +388,8 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
                  err, st, gemm0, gemm1, gemm_flops);
     } else {
     // gather the columns
-    LAUNCH(k_m2l_gather<<<(unsigned)nv, 64, sizeof(cplx) * P, st>>>(nv, p, perm, owner, vidx, B, OI, M,
-                                                                   ws.g_Y.as<cplx>()));
+    LAUNCH(k_m2l_gather<<<(unsigned)((nv * P + 255) / 256), 256, 0, st>>>(nv, p, perm, owner, vidx, B, OI, M,
+                                                                          ws.g_Y.as<cplx>()));
     FMM_CHECK(cudaStreamSynchronize(st));
     // batches and tiles
     std::vector<GemmBatch> bfree, breac;
