@@ -37,8 +37,8 @@ L2_BYTES = 129 * 1024 * 1024
 # the workload, from an ncu capture of the current kernel (None once the
 # kernel changes); the capture command is in the profile summary of the kernel.
 NCU_TRAFFIC = {
-    "three-layer N=32768 p=8 leaf=64": 235.103744e6 + 58.091776e6 + 798.727424e6 + 645.928192e6,
-    "mixed": 1258.536e6 + 754.937088e6,
+    "three-layer N=32768 p=8 leaf=64": 233.948160e6 + 57.788160e6 + 805.450240e6 + 646.008832e6,
+    "mixed": 1258.526e6 + 754.894080e6,
 }
 
 
