@@ -30,7 +30,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="three-layer N=32768 p=8 leaf=64", n=32768, p=8, leaf=64)
+WORKLOADS = {
+    # the configuration the metric is quoted on (default)
+    "three-layer-32768": dict(name="three-layer N=32768 p=8 leaf=64", n=32768, p=8, leaf=64, complex=False),
+    # the large configuration of the mixed-precision form: N = 2^20, p = 10, complex charges
+    "three-layer-1M": dict(name="three-layer N=1048576 p=10 leaf=64 complex charges", n=1048576, p=10, leaf=64,
+                           complex=True),
+}
+WORKLOAD = WORKLOADS["three-layer-32768"]
 METRIC = "FMM particles/sec at rel L2 err 1e-6 (FP64)"
 L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) of the M2L product launches of one evaluation of
@@ -47,6 +54,20 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def aggregate(total_ms, steps, n_per_rank, ws, device):
+    """Whole-job time and throughput: the slowest rank's time of the timed
+    steps (max over ranks), and the units all ranks processed per second
+    (each rank evaluates its own problem of n_per_rank particles)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, ws * n_per_rank / (ms_per_step * 1e-3)
 
 
 def _clock_sampler(path, dev):
@@ -155,11 +176,11 @@ def cpu_oracle_sample(n_targets, seed=0):
         "import sys,time,json;sys.path.insert(0,%r);"
         "from oracle.media import Medium;from oracle import green;"
         "from paper_1902_05132_gb300 import workloads as wl;"
-        "w=wl.three_layer(n=%d,seed=%d,p=%d,leaf=%d);m=Medium(w['k'],w['d'],w['eps']);"
+        "w=wl.three_layer(n=%d,seed=%d,p=%d,leaf=%d,complex_charges=%s);m=Medium(w['k'],w['d'],w['eps']);"
         "sel=wl.sample_targets(len(w['tgt']),%d,seed=3);t=time.perf_counter();"
         "green.direct_sum(m,w['src'],w['q'],w['tgt'],targets=sel);"
         "print(json.dumps({'seconds':time.perf_counter()-t}))"
-    ) % (ROOT, WORKLOAD["n"], seed, WORKLOAD["p"], WORKLOAD["leaf"], n_targets)
+    ) % (ROOT, WORKLOAD["n"], seed, WORKLOAD["p"], WORKLOAD["leaf"], WORKLOAD["complex"], n_targets)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -172,7 +193,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    n_sample = 3
+    n_sample = max(1, 3 * 32768 // WORKLOAD["n"])
     for _ in range(min(args.warmup, 1)):
         cpu_oracle_sample(1)
     vals, secs = [], []
@@ -201,7 +222,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--workload", default="three-layer-32768", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -217,7 +241,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     _build.build()
-    w = workloads.three_layer(n=WORKLOAD["n"], seed=rank, p=WORKLOAD["p"], leaf=WORKLOAD["leaf"])
+    w = workloads.three_layer(n=WORKLOAD["n"], seed=rank, p=WORKLOAD["p"], leaf=WORKLOAD["leaf"],
+                              complex_charges=WORKLOAD["complex"])
     solver = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
     src = torch.tensor(w["src"], device=dev)
     q = torch.tensor(w["q"], device=dev)
@@ -258,14 +283,8 @@ def main():
     if sampler:
         sampler.terminate()
         sampler.wait()
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
     n = len(w["tgt"])
-    value = ws * n / (ms_per_step * 1e-3)
+    ms_per_step, value = aggregate(sum(ms), args.steps, n, ws, dev)
 
     # first evaluation of a fresh solver: translation operators not cached yet
     cold = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
@@ -365,7 +384,7 @@ def main():
     if not args.no_surrogate:
         result["surrogate"] = surrogate_leg(pkg, torch, w, dev, stream)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        n_sample = 6
+        n_sample = max(1, 6 * 32768 // WORKLOAD["n"])      # about 10 s of single-core oracle work
         v, sec = cpu_oracle_sample(n_sample)
         result["cpu_baseline"] = {"value": v, "unit": "particles/s", "cores": 1, "kind": "oracle",
                                   "sample": f"oracle direct sum at {n_sample} sampled targets of the same "
