@@ -61,6 +61,12 @@ extern "C" {
                                  fmm_layered_direct come from the learned
                                  surrogate wherever its held-out check passed
                                  (quadrature elsewhere)                        */
+#define FMM_TEST_STALL_TC (1u << 30) /* test only, with FMM_MIXED: every
+                                 stage of the tensor-core M2L waits for 16
+                                 bytes more than it copies, so its bounded
+                                 waits expire (about 1 s each); the kernel
+                                 then releases its resources and the
+                                 evaluation returns FMM_ERR_TIMEOUT            */
 
 typedef struct fmm_layered fmm_layered_t;
 

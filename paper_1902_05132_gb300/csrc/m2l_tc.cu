@@ -429,7 +429,8 @@ struct TcItem {
 __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items, const unsigned char* __restrict__ Abuf,
                                                const unsigned char* __restrict__ Bbuf,
                                                const int* __restrict__ rexp, const int* __restrict__ isig,
-                                               cplx* __restrict__ Z, int P, int* __restrict__ err) {
+                                               cplx* __restrict__ Z, int P, int* __restrict__ err,
+                                               uint32_t extra_tx) {
   const TcItem it = items[blockIdx.x];
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bars[5];     // full[2], empty[2], done
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
     auto issue = [&](int c, int s) {
       uint32_t base = smem_u32(sm + s * stage_bytes);
       uint32_t bar = smem_u32(&bars[s]);
-      mbar_expect_tx(bar, stage_bytes);
+      mbar_expect_tx(bar, stage_bytes + extra_tx);      // extra_tx: 0 except in the wait-expiry test
       bulk_g2s(base, Ag + (size_t)c * a_bytes, a_bytes, bar);
       bulk_g2s(base + a_bytes, Ag + (size_t)(it.Kc + c) * a_bytes, a_bytes, bar);
       bulk_g2s(base + 2 * a_bytes, Bg + (size_t)c * b_bytes, b_bytes, bar);
@@ -733,7 +734,8 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   FMM_CHECK(cudaEventRecord(gemm0, st));
   if (!items.empty())
     LAUNCH(k_m2l_tc<<<(unsigned)items.size(), 128, smem, st>>>(ditems, Abuf, tc.bbuf.as<unsigned char>(),
-                                                              tc.sbuf.as<int>(), isig, Z, P, err));
+                                                              tc.sbuf.as<int>(), isig, Z, P, err,
+                                                              (h->flags & FMM_TEST_STALL_TC) ? 16u : 0u));
   FMM_CHECK(cudaEventRecord(gemm1, st));
   FMM_CHECK(cudaGetLastError());
   FMM_CHECK(cudaStreamSynchronize(st));       // host tables above go out of scope

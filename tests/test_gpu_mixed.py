@@ -59,3 +59,22 @@ def test_mixed_large_orders(p):
     err = rel_l2(b, a)
     print("two-layer N=600 p=%d: mixed vs FP64 path %.2e" % (p, err))
     assert err < 1e-5
+
+
+def test_tensor_core_wait_expiry_is_reported():
+    # A test-only flag makes every pipeline stage of the tensor-core M2L wait
+    # for bytes that never come: its bounded waits run out, the kernel frees
+    # its tensor memory and returns, and the evaluation reports a timeout.
+    # The context stays usable: a normal evaluation right after is correct.
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    w = workloads.two_layer(n=300, leaf=20, p=5)
+    src, q, tgt = to_dev(torch, w)
+    stalled = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], mixed=True,
+                             extra_flags=pkg.FMM_TEST_STALL_TC)
+    with pytest.raises(pkg.FmmError) as ei:
+        stalled.eval(src, q, tgt)
+    assert ei.value.code == -6 and "bounded wait" in str(ei.value)
+    stalled.close()
+    a, b, _, _ = _pair(torch, w)
+    assert rel_l2(b, a) < 1e-5
