@@ -45,7 +45,7 @@ L2_BYTES = 129 * 1024 * 1024
 # kernel changes); the capture command is in the profile summary of the kernel.
 NCU_TRAFFIC = {
     "three-layer N=32768 p=8 leaf=64": 233.948160e6 + 57.788160e6 + 805.450240e6 + 646.008832e6,
-    "mixed": 1258.526e6 + 754.894080e6,
+    "mixed": None,       # k_m2l_tc changed (coalesced epilogue) after its last capture
 }
 
 
@@ -103,6 +103,15 @@ def _clock_summary(path):
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+def _hbm_peak():
+    """HBM bandwidth: the measured copy figure of this machine, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
 
 
 def _tensor_peak():
@@ -369,16 +378,24 @@ def main():
     tc_flops = mst[-1]["m2l_tensor_flops"]
     bf16_peak, peak_src = _tensor_peak()
     tc_achieved = tc_flops / (tc_ms * 1e-3) / 1e12
+    tc_bytes = mst[-1]["m2l_tc_bytes"]
+    tc_gbs = tc_bytes / (tc_ms * 1e-3) / 1e9
+    hbm_peak, hbm_src = _hbm_peak()
     err_m = float(torch.linalg.vector_norm(out_m - ref_out) / torch.linalg.vector_norm(ref_out))
     result["mixed"] = {
         "value": ws * n / (m_ms * 1e-3), "unit": "particles/s", "ms_per_step": m_ms,
         "rel_l2_vs_fp64_path": err_m, "dtype": "f16 hi/lo -> f32 (M2L), f64 elsewhere",
         "stage_ms": {k: statistics.mean(s["gpu_ms_" + k] for s in mst) for k in keys},
-        "roofline": {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": tc_achieved, "peak": bf16_peak,
-                     "unit": "TFLOP/s", "frac": tc_achieved / bf16_peak, "traffic": NCU_TRAFFIC.get("mixed"),
-                     "kernel_ms": tc_ms, "executed_tflop": tc_flops / 1e12,
-                     "algorithmic_fp64_equiv_tflop": mst[-1]["m2l_gemm_flops"] / 1e12,
-                     "peak_source": peak_src},
+        # the product moves ~70 flop per byte, below the FP16 tensor balance
+        # point (peak flops / HBM bandwidth ~ 280): it is bounded by HBM
+        "roofline": {"bound": "hbm", "kernel": "k_m2l_tc", "achieved": tc_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": tc_gbs / hbm_peak, "traffic": NCU_TRAFFIC.get("mixed"),
+                     "kernel_ms": tc_ms, "algorithmic_gb": tc_bytes / 1e9,
+                     "peak_source": hbm_src,
+                     "tensor": {"achieved": tc_achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                                "frac": tc_achieved / bf16_peak, "executed_tflop": tc_flops / 1e12,
+                                "peak_source": peak_src},
+                     "algorithmic_fp64_equiv_tflop": mst[-1]["m2l_gemm_flops"] / 1e12},
     }
     mixed.close()
     if not args.no_surrogate:

@@ -106,6 +106,10 @@ typedef struct {
   double m2l_tensor_flops; /* FMM_MIXED: flops the tensor cores executed for
                               them (3 real products per tile, padding
                               included); 0 in the FP64 path                  */
+  double m2l_tc_bytes;     /* FMM_MIXED: algorithmic bytes of those products:
+                              the FP16 hi/lo tiles of the gathered columns
+                              and of each operator used, read once, and the
+                              FP64 translated columns written once           */
 } fmm_stats_t;
 
 /*

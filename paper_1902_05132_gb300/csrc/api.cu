@@ -580,6 +580,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   double gemm_flops = 0.0;
   const bool gemm_ran = lo_all[nb] > 0;
   h->stats.m2l_tensor_flops = 0.0;
+  h->stats.m2l_tc_bytes = 0.0;
   run_m2l_gemm(h, nb, (long)lo_all[nb], m2l_lvl, dsched, o_m2l, maxlev, B, OI, loff, ws.vi.as<int>(),
                oc.free_buf.as<cplx>(), oc.rad_buf.as<cplx>(), oc.shift_buf.as<cplx>(), M, L, err, st, E.ev[10],
                E.ev[11], &gemm_flops, cg);
