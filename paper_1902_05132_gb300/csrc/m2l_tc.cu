@@ -514,32 +514,24 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
   __syncthreads();
   tc_fence_after();
   if (!abort_sh) {
-    // Each warp reads its 32 rows (tensor-memory lanes) 16 columns at a time,
-    // scales them, stages them in shared memory (the pipeline buffers are
-    // free once the products are done) and writes them back row-contiguous:
-    // 16 lanes cover 256 consecutive bytes of one row of Z.
     const int m = warp * 32 + lane;               // tile row = tensor-memory lane
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     const int ek = (m < it.rows) ? isig[it.sig_off + m] : 0;
-    constexpr int kStride = 17;                   // padded row of the staging buffer
-    cplx* wb = (cplx*)sm + warp * 32 * kStride;
+    cplx* zr = Z + (it.z_row0 + m) * (long)P + it.z_col0;
     for (int r0 = 0; r0 < it.R16; r0 += 16) {
       float re[16], im[16];
       tmem_ld16(tl + (uint32_t)r0, re);
       tmem_ld16(tl + (uint32_t)(it.R16 + r0), im);
+      if (m < it.rows) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int r = min(r0 + j, it.RB - 1);
-        const int e = rexp[it.scale_off + r] + ek;
-        wb[lane * kStride + j] = C(f32_scaled_to_f64(re[j], e), f32_scaled_to_f64(im[j], e));
+        for (int j = 0; j < 16; ++j) {
+          int r = r0 + j;
+          if (r < it.RB) {
+            const int e = rexp[it.scale_off + r] + ek;
+            zr[r] = C(f32_scaled_to_f64(re[j], e), f32_scaled_to_f64(im[j], e));
+          }
+        }
       }
-      __syncwarp();
-      for (int qq = lane; qq < 32 * 16; qq += 32) {
-        const int row = qq >> 4, col = qq & 15;
-        const int mr = warp * 32 + row, r = r0 + col;
-        if (mr < it.rows && r < it.RB) Z[(it.z_row0 + mr) * (long)P + it.z_col0 + r] = wb[row * kStride + col];
-      }
-      __syncwarp();
     }
   }
   tc_fence_before();
