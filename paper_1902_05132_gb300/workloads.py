@@ -95,3 +95,34 @@ def batched(n_problems=64, seed=0, n_min=10_000, n_max=200_000, p=10, leaf=64):
         out.append(dict(k=k, d=d, eps=eps, p=p, leaf=leaf, src=src, q=q, tgt=src.copy(),
                         name=f"batched problem {i}: N={n}, {L1} layers"))
     return out
+
+
+PAPER_DOMAINS = (((0.0, 0.0, 0.6), 0.10), ((0.0, 0.0, -0.6), 0.15), ((0.0, 0.0, -1.8), 0.05))
+
+
+def _in_domain(rng, n, center, a):
+    """n points uniform inside r(theta) = 0.5 - a + a P_4(cos theta) about
+    `center` (rejection from the enclosing ball of radius 0.5)."""
+    out = []
+    while len(out) < n:
+        p = rng.uniform(-0.5, 0.5, (4 * n, 3))
+        r = np.linalg.norm(p, axis=1)
+        c = np.divide(p[:, 2], r, out=np.zeros_like(r), where=r > 0)
+        p4 = (35 * c ** 4 - 30 * c ** 2 + 3) / 8
+        keep = p[r < 0.5 - a + a * p4]
+        out.extend(keep[: n - len(out)])
+    return np.asarray(out) + np.asarray(center)
+
+
+def paper_domains(counts=(912, 640, 1296), seed=0, p=6, leaf=40):
+    """The paper's shaped test: three layers with interfaces z = 0 and -1.2,
+    k = (1.2, 1.5, 1.8), eps = (1, 2, 3); particles uniform inside the
+    irregular domains r = 0.5 - a + a P_4(cos theta), a = 0.1, 0.15, 0.05,
+    centred at (0, 0, 0.6), (0, 0, -0.6), (0, 0, -1.8) (one per layer);
+    real charges U[0,1]; targets = sources."""
+    rng = np.random.default_rng(seed)
+    src = np.concatenate([_in_domain(rng, m, c, a) for m, (c, a) in zip(counts, PAPER_DOMAINS)])
+    q = rng.uniform(0.0, 1.0, len(src)).astype(complex)
+    n = len(src)
+    return dict(k=[1.2, 1.5, 1.8], d=[0.0, -1.2], eps=[1.0, 2.0, 3.0], p=p, leaf=leaf,
+                src=src, q=q, tgt=src.copy(), name=f"paper domains N={n} p={p} leaf={leaf}")
