@@ -437,7 +437,7 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     FMM_CHECK(cudaMemcpyAsync(dbat, ordered.data(), sizeof(GemmBatch) * ordered.size(), cudaMemcpyHostToDevice, st));
     auto smem_of = [&](int R) { return gemm_smem_max(R); };
     size_t smax = std::max(smem_of(P), std::max(smem_of(np), nm ? smem_of(nm) : (size_t)0));
-    cudaFuncSetAttribute(k_zgemm_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    FMM_CHECK(cudaFuncSetAttribute(k_zgemm_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     *gemm_flops = 8.0 * macs;
     FMM_CHECK(cudaEventRecord(gemm0, st));
     if (!bfree.empty())

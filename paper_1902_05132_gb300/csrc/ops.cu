@@ -662,7 +662,7 @@ void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const d
   long ne = (long)g.Q * nr;
   LAUNCH(k_reac_bessel<<<(ne + 127) / 128, 128, 0, st>>>(p, g.Q, nn, nr, d_rho, R.kr.as<cplx>(), Jc, Jr));
   size_t smem = sizeof(double) * (2 * TQR * (FMM_MAXP + 1) + 2 * TQR * P + 2 * TQR * D);
-  cudaFuncSetAttribute(k_reac_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  FMM_CHECK(cudaFuncSetAttribute(k_reac_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int threads = 256;
   dim3 grid(nr, 2 * p + 1, ((p + 1) * P + 8 * threads - 1) / (8 * threads));
   LAUNCH(k_reac_contract<<<grid, threads, smem, st>>>(p, g.Q, nn, Ac, Bc, Ar, Br, Jc, Jr, d_out_off, ops));
@@ -674,7 +674,7 @@ void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs,
   const size_t per = sizeof(cplx) * P + sizeof(double) * (p + 1 + 4);
   int chunk = std::min(16, (int)((200 * 1024) / per));
   size_t smem = per * chunk;
-  cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  FMM_CHECK(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (n) LAUNCH(k_p2m<<<n, 128, smem, st>>>(p, chunk, leaves, B, cgs, spos, sq, M));
 }
 
