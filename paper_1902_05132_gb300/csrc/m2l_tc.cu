@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
                                                const unsigned char* __restrict__ Bbuf,
                                                const int* __restrict__ rexp, const int* __restrict__ isig,
                                                cplx* __restrict__ Z, int P, int* __restrict__ err,
-                                               uint32_t extra_tx) {
+                                               uint32_t extra_tx, int nst) {
   const TcItem it = items[blockIdx.x];
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bars[5];     // full[2], empty[2], done
@@ -471,11 +471,12 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
       ++issued[s];
     };
     bool ok = true;
+    // nst (1 or 2) pipeline stages: chunk c goes through stage c % nst
     issue(0, 0);
-    if (it.Kc > 1) issue(1, 1);
+    if (nst > 1 && it.Kc > 1) issue(1, 1);
     for (int c = 0; c < it.Kc; ++c) {
-      const int s = c & 1;
-      const uint32_t ph = (uint32_t)(c >> 1) & 1u;
+      const int s = c % nst;
+      const uint32_t ph = (uint32_t)(c / nst) & 1u;
       if (!mbar_wait(smem_u32(&bars[s]), ph)) { ok = false; break; }
       ++landed[s];
       tc_fence_after();
@@ -490,9 +491,9 @@ __global__ void __launch_bounds__(128) k_m2l_tc(const TcItem* __restrict__ items
         umma_f16(tmem, al, bh, idesc, 1u);
       }
       umma_commit(smem_u32(&bars[2 + s]));
-      if (c + 2 < it.Kc) {
+      if (c + nst < it.Kc) {
         if (!mbar_wait(smem_u32(&bars[2 + s]), ph)) { ok = false; break; }
-        issue(c + 2, s);
+        issue(c + nst, s);
       }
     }
     umma_commit(smem_u32(&bars[4]));
@@ -739,13 +740,19 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   FMM_CHECK(cudaMemcpyAsync(ditems, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice, st));
   int max_np = 16;
   for (const TcItem& t : items) max_np = std::max(max_np, t.N_pad);
-  const size_t smem = 1024 + 2 * (2 * (size_t)kTileM * kRowBytes + 2 * (size_t)max_np * kRowBytes);
+  // two pipeline stages when two CTAs still fit on an SM; otherwise one
+  // stage, so that two CTAs share the SM and one's epilogue overlaps the
+  // other's copies and products (228 KB per SM, 1 KB reserved per CTA)
+  const size_t stage = 2 * (size_t)kTileM * kRowBytes + 2 * (size_t)max_np * kRowBytes;
+  const size_t per_sm = 228 * 1024;
+  const int nst = (2 * (2 * stage + 2048) <= per_sm) ? 2 : ((2 * (stage + 2048) <= per_sm) ? 1 : 2);
+  const size_t smem = 1024 + nst * stage;
   FMM_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FMM_CHECK(cudaEventRecord(gemm0, st));
   if (!items.empty())
     LAUNCH(k_m2l_tc<<<(unsigned)items.size(), 128, smem, st>>>(ditems, Abuf, tc.bbuf.as<unsigned char>(),
                                                               tc.sbuf.as<int>(), isig, Z, P, err,
-                                                              (h->flags & FMM_TEST_STALL_TC) ? 16u : 0u));
+                                                              (h->flags & FMM_TEST_STALL_TC) ? 16u : 0u, nst));
   FMM_CHECK(cudaEventRecord(gemm1, st));
   FMM_CHECK(cudaGetLastError());
   FMM_CHECK(cudaStreamSynchronize(st));       // host tables above go out of scope
