@@ -297,43 +297,34 @@ __global__ void k_inverse_perm(long n, const int* __restrict__ perm, int* __rest
 static size_t gemm_smem(int RB, int CB, int TK) {
   return sizeof(cplx) * ((size_t)RB * CB + (size_t)TK * Z_KB * CB);
 }
-// Shared memory per CTA: preferably at most ~110 KB, so that two CTAs share
-// an SM (a large operator then runs as row blocks); up to 200 KB when no
-// resident row block fits the smaller size.
-static const size_t kGemmSmemPref = 110 * 1024;
 static const size_t kGemmSmemCap = 200 * 1024;
 // Thread columns of a block of RB rows: as many as 128 threads allow, fewer
 // if the input tile would not fit beside the operator block.
-static int gemm_tk(int RB, int CB, size_t cap) {
+static int gemm_tk(int RB, int CB) {
   int TK = 128 / ((RB + Z_RPT - 1) / Z_RPT);
-  while (TK > 1 && gemm_smem(RB, CB, TK) > cap) --TK;
+  while (TK > 1 && gemm_smem(RB, CB, TK) > kGemmSmemCap) --TK;
   return TK;
 }
 // Tile of an R x R operator: the whole operator resident if it fits, else
 // row blocks of it (each resident), else 96-row blocks streamed in chunks
 // of the contraction.  Every block, the ragged last one included, fits.
-static void gemm_tiles(int R, int& RB, int& CB, size_t& cap_used) {
+static void gemm_tiles(int R, int& RB, int& CB) {
   auto full_tk = [](int rb) { return 128 / ((rb + Z_RPT - 1) / Z_RPT); };
+  RB = std::min(R, 3 * 128);
   CB = R;
-  for (size_t cap : {kGemmSmemPref, kGemmSmemCap}) {
-    RB = std::min(R, 3 * 128);
-    while (RB > 3 && gemm_smem(RB, CB, full_tk(RB)) > cap) RB -= 3;
-    cap_used = cap;
-    if (gemm_smem(RB, CB, full_tk(RB)) <= cap) return;
-  }
-  cap_used = kGemmSmemCap;
+  while (RB > 3 && gemm_smem(RB, CB, full_tk(RB)) > kGemmSmemCap) RB -= 3;
+  if (gemm_smem(RB, CB, full_tk(RB)) <= kGemmSmemCap) return;
   RB = std::min(R, 96);
   CB = (int)(kGemmSmemCap / gemm_smem(RB, 1, full_tk(RB)));
 }
 // Largest shared memory of any block of an R x R operator.
 static size_t gemm_smem_max(int R) {
   int RB, CB;
-  size_t cap;
-  gemm_tiles(R, RB, CB, cap);
+  gemm_tiles(R, RB, CB);
   size_t m = 0;
   for (int r0 = 0; r0 < R; r0 += RB) {
     int rb = std::min(RB, R - r0);
-    m = std::max(m, gemm_smem(rb, CB, gemm_tk(rb, CB, cap)));
+    m = std::max(m, gemm_smem(rb, CB, gemm_tk(rb, CB)));
   }
   return m;
 }
@@ -415,10 +406,9 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
       std::vector<GemmBatch>& dst = reac ? breac : bfree;
       auto add = [&](long a_off, int R, long yz) {
         int RB, CB;
-        size_t cap;
-        gemm_tiles(R, RB, CB, cap);
+        gemm_tiles(R, RB, CB);
         for (int r0 = 0; r0 < R; r0 += RB) {
-          const int rb = std::min(RB, R - r0), tk = gemm_tk(rb, CB, cap);
+          const int rb = std::min(RB, R - r0), tk = gemm_tk(rb, CB);
           // column chunks of about 128, a whole number of column tiles (tk * Z_KB)
           const int kt = tk * Z_KB, chunk = std::max(kt, (128 / kt) * kt);
           for (int c0 = 0; c0 < K; c0 += chunk) {
