@@ -27,8 +27,10 @@
 // rows (MMA N = 2 x 16-rounded output rows) are operand B.  Global copies are
 // stored already swizzled in chunks of 64 contraction entries, so one bulk
 // copy per chunk lands each operand in shared memory in the form the tensor
-// core reads.  Chunks go through a two-stage pipeline fed by cp.async.bulk
-// and mbarriers; every wait is bounded.
+// core reads.  Chunks go through a one- or two-stage pipeline fed by
+// cp.async.bulk and mbarriers (one stage when that lets two CTAs share an SM,
+// so that one CTA's epilogue overlaps the other's copies and products); every
+// wait is bounded.
 #include <cuda_fp16.h>
 
 #include <algorithm>
