@@ -170,7 +170,8 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
                   &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,
-                  &h->tc.bbuf, &h->tc.sbuf, &h->tc.phase_f};
+                  &ws.rot_info, &ws.rot_jobs, &ws.rot_bat, &ws.rot_rs,
+                  &h->tc.bbuf, &h->tc.sbuf, &h->tc.phase_f, &h->rot.w, &h->rot.az_buf};
   for (DevBuf* b : gb) b->release();
   h->cache.free_buf.release();
   h->cache.shift_buf.release();

@@ -117,6 +117,8 @@ struct Workspace {
   DevBuf g_owner, g_keys, g_vals, g_inv, g_Y, g_Z, g_runs, g_bat;
   // tensor-core M2L (mixed precision): run tables, operand tiles, scales, work items
   DevBuf tc_runs, tc_jobs, tc_a, tc_sig, tc_parts, tc_items, tc_etab;
+  // rotation-form free-space M2L: run info, operator jobs, batches, run starts
+  DevBuf rot_info, rot_jobs, rot_bat, rot_rs;
   DevBuf out_tmp;
   DevBuf cub_tmp;
 };
@@ -150,6 +152,15 @@ struct TcCache {
   std::vector<bool> pending_reac;
 };
 
+// Rotation form of the free-space M2L: rotation matrices of the 343 offset
+// directions and the coaxial operators keyed by (k, box width, |offset|^2).
+struct RotCache {
+  bool ready = false;
+  DevBuf w, az_buf;
+  long az_used = 0;
+  std::map<std::tuple<uint64_t, uint64_t, int>, long> az;
+};
+
 // Learned surrogate of the reaction components: training data, networks and
 // the per-cell verdict of the held-out check.
 struct SurrState {
@@ -176,6 +187,7 @@ struct fmm_layered {
   Workspace ws;
   OpCache cache;
   TcCache tc;
+  RotCache rot;
   SurrState surr;
   fmm_stats_t stats{};
   std::string err;

@@ -335,6 +335,11 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
                 const cplx* M, cplx* Z, int* err, cudaStream_t st, cudaEvent_t gemm0, cudaEvent_t gemm1,
                 double* gemm_flops);
 
+void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector<long>& col0,
+                 const std::vector<int>& cnt, const int* d_rs, int nruns, const int* perm, const int* owner,
+                 const int* vidx, BoxGeom B, const std::vector<CompGeom>& cgh, const cplx* Y, cplx* Z,
+                 double* macs, cudaEvent_t ev_start, cudaStream_t st);
+
 // Host driver: all V pairs of all levels.  L receives the M2L part for every
 // box with targets at level >= 2; then L2L level by level.
 void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
@@ -395,6 +400,10 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     std::vector<GemmBatch> bfree, breac;
     long k0 = 0;
     double macs = 0.0;       // complex multiply-adds of the translations (operator entries x columns)
+    // free-space classes in rotation form from p = 5 on (2.7x fewer products at p = 8)
+    const bool use_rot = p >= 5;
+    std::vector<int> rot_runs, rot_cnt;
+    std::vector<long> rot_col0;
     for (int r = 0; r < nruns; ++r) {
       long off = (long)(hk[r] >> 1);
       bool reac = hk[r] & 1;
@@ -420,7 +429,11 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
           }
         }
       };
-      if (!reac) {
+      if (!reac && use_rot) {
+        rot_runs.push_back(r);
+        rot_col0.push_back(k0);
+        rot_cnt.push_back(K);
+      } else if (!reac) {
         add(off, P, 0);
         macs += (double)K * P * P;
       } else {
@@ -438,8 +451,17 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     auto smem_of = [&](int R) { return gemm_smem_max(R); };
     size_t smax = std::max(smem_of(P), std::max(smem_of(np), nm ? smem_of(nm) : (size_t)0));
     FMM_CHECK(cudaFuncSetAttribute(k_zgemm_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    if (!rot_runs.empty()) {
+      std::vector<int> rs(nruns + 1, 0);
+      for (int r = 0; r < nruns; ++r) rs[r + 1] = rs[r] + hc[r];
+      int* d_rs = (int*)tc_need(ws.rot_rs, sizeof(int) * rs.size() + 64);
+      FMM_CHECK(cudaMemcpyAsync(d_rs, rs.data(), sizeof(int) * rs.size(), cudaMemcpyHostToDevice, st));
+      run_m2l_rot(h, rot_runs, rot_col0, rot_cnt, d_rs, nruns, perm, owner, vidx, B, cgh, ws.g_Y.as<cplx>(),
+                  ws.g_Z.as<cplx>(), &macs, gemm0, st);
+    } else {
+      FMM_CHECK(cudaEventRecord(gemm0, st));
+    }
     *gemm_flops = 8.0 * macs;
-    FMM_CHECK(cudaEventRecord(gemm0, st));
     if (!bfree.empty())
       LAUNCH(k_zgemm_res<<<(unsigned)bfree.size(), 128, smem_of(P), st>>>(dbat, free_ops, ws.g_Y.as<cplx>(),
                                                                           ws.g_Z.as<cplx>()));

@@ -1,0 +1,295 @@
+// Free-space M2L in rotation form (O(p^3) per translation).
+//
+// The free-space translation L = A(b) M of Thm. 2.3 / eq. metole for a centre
+// offset b factors through a rotation Q that takes b to |b| z:
+//     A(b) = W^T A(|b| z) conj(W),
+// where W is block diagonal in the degree n with
+//     Y_n^m(Q x) = sum_m' W[(n,m),(n,m')] Y_n^m'(x)        (|x| = 1),
+// and the coaxial operator A(|b| z) couples only equal orders m (the
+// harmonic Y_q^{mu-m} of the Gaunt formula vanishes on the z axis unless
+// mu = m).  Per translation this costs 2 sum_n (2n+1)^2 + sum_m (p+1-|m|)^2
+// complex multiply-adds instead of (p+1)^4 (2,427 instead of 6,561 at p = 8).
+// W is computed once per handle for the 343 offset directions of the V
+// lists by a product quadrature on the sphere (Gauss-Legendre in cos theta,
+// equispaced in phi), exact for these polynomials; A(|b| z) comes from the
+// same Gaunt-formula kernel as the dense operators and is cached per
+// (k, box width, |offset|^2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fmm_internal.h"
+
+void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st);
+
+namespace {
+
+__host__ __device__ inline long rot_nw(int p) { return (long)(p + 1) * (2 * p + 1) * (2 * p + 3) / 3; }
+__host__ __device__ inline int rot_ob(int n) { return n * (2 * n - 1) * (2 * n + 1) / 3; }   // start of block n
+__host__ __device__ inline int rot_naz(int p) { return (p + 1) * (2 * (p + 1) * (p + 1) + 1) / 3; }
+// start of the order-m block of the compact coaxial operator (m = -p..p)
+__host__ __device__ inline int rot_om(int p, int m) {
+  int o = 0;
+  for (int j = -p; j < m; ++j) o += (p + 1 - abs(j)) * (p + 1 - abs(j));
+  return o;
+}
+__device__ inline int deg_full(int i) {
+  int n = (int)sqrtf((float)i);
+  while ((n + 1) * (n + 1) <= i) ++n;
+  while (n * n > i) --n;
+  return n;
+}
+
+// Y_n^m at the quadrature points, plain (slot -1, stored last) and rotated by
+// the Q of every direction slot: Ybuf[(slot or 343)][pt][(n,m)].
+__global__ void k_rot_y(int p, int npt, int nphi, const double* __restrict__ xg, cplx* __restrict__ Ybuf) {
+  const int slot = blockIdx.y;                 // 0..342 directions, 343: unrotated
+  const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npt) return;
+  const int P = (p + 1) * (p + 1);
+  const double ct0 = xg[pt / nphi], st0 = sqrt(fmax(0.0, 1.0 - ct0 * ct0));
+  const double ph0 = 2.0 * FMM_PI * (pt % nphi) / nphi;
+  double x[3] = {st0 * cos(ph0), st0 * sin(ph0), ct0};
+  if (slot < 343) {
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    double r = sqrt((double)(dx * dx + dy * dy + dz * dz));
+    if (r > 0) {
+      // Q = R_y(-theta) R_z(-phi) maps the direction (theta, phi) to +z
+      double th = acos(fmin(1.0, fmax(-1.0, dz / r))), ph = atan2((double)dy, (double)dx);
+      double cp = cos(ph), sp = sin(ph), cth = cos(th), sth = sin(th);
+      double a0 = cp * x[0] + sp * x[1], a1 = -sp * x[0] + cp * x[1], a2 = x[2];
+      x[0] = cth * a0 - sth * a2;
+      x[1] = a1;
+      x[2] = sth * a0 + cth * a2;
+    }
+  }
+  double ct = fmin(1.0, fmax(-1.0, x[2]));
+  double st = sqrt(x[0] * x[0] + x[1] * x[1]);
+  double phi = atan2(x[1], x[0]);
+  double Pa[(FMM_MAXP + 1) * (FMM_MAXP + 2) / 2];
+  phat_real(p, ct, st, Pa);
+  cplx* Y = Ybuf + ((long)slot * npt + pt) * P;
+  for (int n = 0; n <= p; ++n)
+    for (int m = -n; m <= n; ++m) {
+      int am = abs(m);
+      double v = Pa[n * (n + 1) / 2 + am] * ((m < 0 && (am & 1)) ? -1.0 : 1.0);
+      double s, c;
+      sincos(m * phi, &s, &c);
+      Y[n * n + n + m] = C(v * c, v * s);
+    }
+}
+
+// W of every slot: W[slot][ob(n) + (m+n)(2n+1) + (m'+n)] = sum_pt w_pt Y_n^m(Q x_pt) conj(Y_n^m'(x_pt))
+__global__ void k_rot_w(int p, int npt, const double* __restrict__ wpt, const cplx* __restrict__ Ybuf,
+                        cplx* __restrict__ Wall) {
+  const int slot = blockIdx.x;
+  const int P = (p + 1) * (p + 1);
+  const long NW = rot_nw(p);
+  const cplx* Yq = Ybuf + (long)slot * npt * P;
+  const cplx* Yx = Ybuf + (long)343 * npt * P;
+  for (long e = threadIdx.x; e < NW; e += blockDim.x) {
+    int n = 0;
+    while (rot_ob(n + 1) <= e) ++n;
+    const int loc = (int)(e - rot_ob(n)), w2 = 2 * n + 1;
+    const int m = loc / w2 - n, mp = loc % w2 - n;
+    cplx acc = C(0, 0);
+    for (int q = 0; q < npt; ++q) cfma(acc, cscale(Yq[(long)q * P + n * n + n + m], wpt[q]), cconj(Yx[(long)q * P + n * n + n + mp]));
+    Wall[(long)slot * NW + e] = acc;
+  }
+}
+
+// operator slot of each run: direction index of its first pair's offset
+__global__ void k_run_slot(int nruns, const int* __restrict__ rs, const int* __restrict__ perm,
+                           const int* __restrict__ owner, const int* __restrict__ vidx, BoxGeom B,
+                           int* __restrict__ out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  int e = perm[rs[r]];
+  int T = owner[e], S = vidx[e];
+  const int* ct = B.coord + 3 * T;
+  const int* cs = B.coord + 3 * S;
+  int dx = ct[0] - cs[0], dy = ct[1] - cs[1], dz = ct[2] - cs[2];
+  out[3 * r] = ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
+  out[3 * r + 1] = B.comp[T];
+  out[3 * r + 2] = B.lev[T];
+}
+
+}  // namespace
+
+struct RotBatch {
+  long col0;         // translated-column index of the first pair
+  long az_off;       // dense coaxial operator (input-major, P x P)
+  int K;             // pairs in this batch (<= the kernel's column tile)
+  int slot;          // direction slot (W)
+};
+
+// Z[col] = W^T A_z conj(W) Y[col] for the columns of one batch (one CTA).
+__global__ void __launch_bounds__(128) k_zrot(int p, int KC, const RotBatch* __restrict__ batches,
+                                              const cplx* __restrict__ Wall, const cplx* __restrict__ az_ops,
+                                              const cplx* __restrict__ Y, cplx* __restrict__ Z) {
+  const RotBatch bt = batches[blockIdx.x];
+  const int P = (p + 1) * (p + 1);
+  const int NW = (int)rot_nw(p), NAZ = rot_naz(p);
+  extern __shared__ cplx sm[];
+  cplx* Wc = sm;                  // [NW]
+  cplx* Az = Wc + NW;             // [NAZ] compact, order-m blocks of (p+1-|m|)^2, row = output degree
+  cplx* T0 = Az + NAZ;            // [KC][P]
+  cplx* T1 = T0 + (size_t)KC * P; // [KC][P]
+  __shared__ int om[2 * FMM_MAXP + 1];
+  for (int m = threadIdx.x - p; m <= p; m += blockDim.x) om[m + p] = rot_om(p, m);
+  const cplx* Wg = Wall + (long)bt.slot * NW;
+  for (int e = threadIdx.x; e < NW; e += blockDim.x) Wc[e] = Wg[e];
+  const cplx* A = az_ops + bt.az_off;
+  __syncthreads();
+  for (int m = -p; m <= p; ++m) {
+    const int am = abs(m), nb = p + 1 - am, o = om[m + p];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int n = am + e / nb, np_ = am + e % nb;                 // output n, input n'
+      Az[o + e] = A[(long)(np_ * np_ + np_ + m) * P + (n * n + n + m)];
+    }
+  }
+  for (int e = threadIdx.x; e < bt.K * P; e += blockDim.x) T0[e] = Y[(bt.col0 + e / P) * (long)P + e % P];
+  __syncthreads();
+  // conj(W): rotate the multipole expansion into the frame of the offset
+  for (int e = threadIdx.x; e < bt.K * P; e += blockDim.x) {
+    const int k = e / P, i = e % P, n = deg_full(i), m = i - n * n - n, w2 = 2 * n + 1;
+    const cplx* wr = Wc + rot_ob(n) + (m + n) * w2;
+    const cplx* x = T0 + k * P + n * n;
+    cplx acc = C(0, 0);
+    for (int j = 0; j < w2; ++j) cfma(acc, cconj(wr[j]), x[j]);
+    T1[e] = acc;
+  }
+  __syncthreads();
+  // coaxial translation, order by order
+  for (int e = threadIdx.x; e < bt.K * P; e += blockDim.x) {
+    const int k = e / P, i = e % P, n = deg_full(i), m = i - n * n - n, am = abs(m), nb = p + 1 - am;
+    const cplx* ar = Az + om[m + p] + (n - am) * nb;
+    const cplx* x = T1 + k * P;
+    cplx acc = C(0, 0);
+    for (int j = 0; j < nb; ++j) {
+      const int np_ = am + j;
+      cfma(acc, ar[j], x[np_ * np_ + np_ + m]);
+    }
+    T0[e] = acc;
+  }
+  __syncthreads();
+  // W^T: back to the original frame
+  for (int e = threadIdx.x; e < bt.K * P; e += blockDim.x) {
+    const int k = e / P, i = e % P, n = deg_full(i), m = i - n * n - n, w2 = 2 * n + 1;
+    const cplx* wc = Wc + rot_ob(n) + (m + n);
+    const cplx* x = T0 + k * P + n * n;
+    cplx acc = C(0, 0);
+    for (int j = 0; j < w2; ++j) cfma(acc, wc[j * w2], x[j]);
+    Z[(bt.col0 + k) * (long)P + i] = acc;
+  }
+}
+
+// W tables of the handle (once).
+static void rot_tables(fmm_layered* h, cudaStream_t st) {
+  RotCache& R = h->rot;
+  if (R.ready) return;
+  const int p = h->p, P = (p + 1) * (p + 1);
+  std::vector<double> xg, wg;
+  gauss_legendre_pub(p + 2, xg, wg);
+  const int nphi = 2 * p + 2, npt = (p + 2) * nphi;
+  std::vector<double> wpt(npt);
+  for (int i = 0; i < npt; ++i) wpt[i] = wg[i / nphi] * 2.0 * FMM_PI / nphi;
+  DevBuf dx, dw, ybuf;
+  dx.ensure(sizeof(double) * xg.size());
+  dw.ensure(sizeof(double) * npt);
+  ybuf.ensure(sizeof(cplx) * (size_t)344 * npt * P);
+  FMM_CHECK(cudaMemcpyAsync(dx.ptr, xg.data(), sizeof(double) * xg.size(), cudaMemcpyHostToDevice, st));
+  FMM_CHECK(cudaMemcpyAsync(dw.ptr, wpt.data(), sizeof(double) * npt, cudaMemcpyHostToDevice, st));
+  R.w.ensure(sizeof(cplx) * (size_t)343 * rot_nw(p));
+  LAUNCH(k_rot_y<<<dim3((npt + 63) / 64, 344), 64, 0, st>>>(p, npt, nphi, dx.as<double>(), ybuf.as<cplx>()));
+  LAUNCH(k_rot_w<<<343, 128, 0, st>>>(p, npt, dw.as<double>(), ybuf.as<cplx>(), R.w.as<cplx>()));
+  FMM_CHECK(cudaGetLastError());
+  FMM_CHECK(cudaStreamSynchronize(st));      // the temporary buffers are freed on return
+  R.ready = true;
+}
+
+static uint64_t rbits(double x) {
+  uint64_t u;
+  memcpy(&u, &x, 8);
+  return u;
+}
+
+// Free-space runs of the sorted V pairs through the rotation form: Z for
+// every pair of the runs listed (run index r, its first column and count).
+void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector<long>& col0,
+                 const std::vector<int>& cnt, const int* d_rs, int nruns, const int* perm, const int* owner,
+                 const int* vidx, BoxGeom B, const std::vector<CompGeom>& cgh, const cplx* Y, cplx* Z,
+                 double* macs, cudaEvent_t ev_start, cudaStream_t st) {
+  if (runs.empty()) {
+    FMM_CHECK(cudaEventRecord(ev_start, st));
+    return;
+  }
+  Workspace& ws = h->ws;
+  RotCache& R = h->rot;
+  const int p = h->p, P = (p + 1) * (p + 1);
+  rot_tables(h, st);
+  // slot, component and level of every run
+  int* d_info = (int*)tc_need(ws.rot_info, sizeof(int) * 3 * (size_t)nruns + 64);
+  LAUNCH(k_run_slot<<<(nruns + 127) / 128, 128, 0, st>>>(nruns, d_rs, perm, owner, vidx, B, d_info));
+  std::vector<int> info(3 * (size_t)nruns);
+  FMM_CHECK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * info.size(), cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaStreamSynchronize(st));
+  // coaxial operators (k, w, |d|^2), built on first use
+  std::vector<SepJob> jobs;
+  auto az_of = [&](int comp, int lev, int slot) -> long {
+    const double k = cgh[comp].kt, w = cgh[comp].h2 / (double)(1 << lev);
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    const int d2 = dx * dx + dy * dy + dz * dz;
+    auto key = std::make_tuple(rbits(k), rbits(w), d2);
+    auto it = R.az.find(key);
+    if (it != R.az.end()) return it->second;
+    long off = R.az_used;
+    R.az_used += (long)P * P;
+    R.az[key] = off;
+    SepJob j{};
+    j.b[0] = 0.0;
+    j.b[1] = 0.0;
+    j.b[2] = std::sqrt((double)d2) * w;
+    j.k = k;
+    j.kind = 0;
+    j.out_off = off;
+    jobs.push_back(j);
+    return off;
+  };
+  const int NW = (int)rot_nw(p), NAZ = rot_naz(p);
+  const size_t fixed = sizeof(cplx) * (size_t)(NW + NAZ);
+  int KC = (int)std::min<size_t>(32, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / (2 * sizeof(cplx) * P));
+  KC = std::max(KC, 1);
+  std::vector<RotBatch> bat;
+  for (size_t i = 0; i < runs.size(); ++i) {
+    const int r = runs[i];
+    const int slot = info[3 * r], comp = info[3 * r + 1], lev = info[3 * r + 2];
+    const long az = az_of(comp, lev, slot);
+    for (int c0 = 0; c0 < cnt[i]; c0 += KC) {
+      RotBatch b{};
+      b.col0 = col0[i] + c0;
+      b.az_off = az;
+      b.K = std::min(KC, cnt[i] - c0);
+      b.slot = slot;
+      bat.push_back(b);
+    }
+    *macs += (double)cnt[i] * (2.0 * NW + NAZ);
+  }
+  if (!jobs.empty()) {
+    R.az_buf.grow_keep(sizeof(cplx) * (size_t)R.az_used, sizeof(cplx) * (size_t)(R.az_used - (long)jobs.size() * P * P),
+                       st);
+    SepJob* dj = (SepJob*)tc_need(ws.rot_jobs, sizeof(SepJob) * jobs.size() + 64);
+    FMM_CHECK(cudaMemcpyAsync(dj, jobs.data(), sizeof(SepJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+    launch_sep_ops(p, dj, (int)jobs.size(), h->tab.gaunt.as<double>(), R.az_buf.as<cplx>(), st);
+    FMM_CHECK(cudaGetLastError());
+  }
+  RotBatch* db = (RotBatch*)tc_need(ws.rot_bat, sizeof(RotBatch) * bat.size() + 64);
+  FMM_CHECK(cudaMemcpyAsync(db, bat.data(), sizeof(RotBatch) * bat.size(), cudaMemcpyHostToDevice, st));
+  const size_t smem = fixed + 2 * sizeof(cplx) * (size_t)KC * P;
+  FMM_CHECK(cudaFuncSetAttribute(k_zrot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FMM_CHECK(cudaEventRecord(ev_start, st));   // the translation launches start here
+  LAUNCH(k_zrot<<<(unsigned)bat.size(), 128, smem, st>>>(p, KC, db, R.w.as<cplx>(), R.az_buf.as<cplx>(), Y, Z));
+  FMM_CHECK(cudaGetLastError());
+}
