@@ -348,7 +348,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_zrot + k_zgemm_res", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "per": "the M2L product launches of one evaluation (free-space and reaction classes)",
+                     "per": "the M2L translation launches of one evaluation (free-space and reaction classes)",
                      "kernel_ms": gemm_ms, "algorithmic_tflop": gemm_flops / 1e12,
                      "peak_source": "FP64 FMA throughput measured on this GPU by the library's probe (of measured)"},
         "stage_ms": mean_stage,

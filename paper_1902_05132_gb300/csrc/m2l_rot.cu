@@ -260,7 +260,11 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
   };
   const int NW = (int)rot_nw(p), NAZ = rot_naz(p);
   const size_t fixed = sizeof(cplx) * (size_t)(NW + NAZ);
-  int KC = (int)std::min<size_t>(32, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / (2 * sizeof(cplx) * P));
+  // column tile: up to 32 columns within ~110 KB (two CTAs per SM) when at
+  // least 8 columns fit there, else within 200 KB
+  const size_t col_bytes = 2 * sizeof(cplx) * P;
+  int KC = (int)std::min<size_t>(32, (110 * 1024 - std::min<size_t>(fixed, 110 * 1024)) / col_bytes);
+  if (KC < 8) KC = (int)std::min<size_t>(32, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / col_bytes);
   KC = std::max(KC, 1);
   std::vector<RotBatch> bat;
   for (size_t i = 0; i < runs.size(); ++i) {
