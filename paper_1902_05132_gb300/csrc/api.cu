@@ -26,7 +26,11 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
                   const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
                   const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
                   const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
-                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh);
+                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh,
+                  const long* l2l_rot_tab);
+void rot_shift_tables(fmm_layered* h, const std::vector<CompGeom>& cgh, const std::vector<std::vector<char>>& has_level,
+                      int maxlev, std::vector<long>& m2m_az, std::vector<long>& l2l_az, cudaStream_t st);
+void launch_m2m_rot(fmm_layered* h, const int* boxes, int n, BoxGeom B, const long* az_tab, cplx* M, cudaStream_t st);
 void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
                       int* err, cudaStream_t st);
 void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* tpos,
@@ -170,7 +174,7 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
                   &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,
-                  &ws.rot_info, &ws.rot_jobs, &ws.rot_bat, &ws.rot_rs,
+                  &ws.rot_info, &ws.rot_jobs, &ws.rot_bat, &ws.rot_rs, &ws.rot_tab,
                   &h->tc.bbuf, &h->tc.sbuf, &h->tc.phase_f, &h->rot.w, &h->rot.az_buf};
   for (DevBuf* b : gb) b->release();
   h->cache.free_buf.release();
@@ -527,6 +531,16 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.n_reac_classes = n_classes;
   h->stats.n_free_ops = (long)sep_free.size();
   h->stats.n_reac_T_nodes = t_nodes;
+  // shifts in rotation form (p >= 5): coaxial operators per (component, level)
+  const bool rot_shifts = p >= 5;
+  long* d_rot_tab = nullptr;
+  if (rot_shifts) {
+    std::vector<long> m2m_az, l2l_az;
+    rot_shift_tables(h, cg, has_level, maxlev, m2m_az, l2l_az, st);
+    m2m_az.insert(m2m_az.end(), l2l_az.begin(), l2l_az.end());
+    d_rot_tab = (long*)tc_need(ws.rot_tab, sizeof(long) * m2m_az.size() + 64);
+    FMM_CHECK(cudaMemcpyAsync(d_rot_tab, m2m_az.data(), sizeof(long) * m2m_az.size(), cudaMemcpyHostToDevice, st));
+  }
   E.mark(2, st);
   // ---- passes
   auto t2 = Clock::now();
@@ -567,8 +581,10 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaMemsetAsync(err, 0, 4, st));
   // upward pass
   launch_p2m(p, dsched + o_p2m, (int)p2m_leaves.size(), B, dcg, ws.spos.as<double>(), ws.sq.as<cplx>(), M, st);
-  for (int l = maxlev; l >= 2; --l)
-    launch_m2m(p, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, dtabs, oc.shift_buf.as<cplx>(), M, st);
+  for (int l = maxlev; l >= 2; --l) {
+    if (rot_shifts) launch_m2m_rot(h, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, d_rot_tab, M, st);
+    else launch_m2m(p, dsched + o_m2m[l], (int)m2m_lvl[l].size(), B, dtabs, oc.shift_buf.as<cplx>(), M, st);
+  }
   FMM_CHECK(cudaGetLastError());
   E.mark(3, st);
   // downward pass
@@ -584,7 +600,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.m2l_tc_bytes = 0.0;
   run_m2l_gemm(h, nb, (long)lo_all[nb], m2l_lvl, dsched, o_m2l, maxlev, B, OI, loff, ws.vi.as<int>(),
                oc.free_buf.as<cplx>(), oc.rad_buf.as<cplx>(), oc.shift_buf.as<cplx>(), M, L, err, st, E.ev[10],
-               E.ev[11], &gemm_flops, cg);
+               E.ev[11], &gemm_flops, cg, rot_shifts ? d_rot_tab + (size_t)nc * 23 : nullptr);
   FMM_CHECK(cudaGetLastError());
   E.mark(4, st);
   long NT = comps.empty() ? 0 : comps.back().to + comps.back().nt;

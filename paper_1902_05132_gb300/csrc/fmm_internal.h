@@ -118,7 +118,7 @@ struct Workspace {
   // tensor-core M2L (mixed precision): run tables, operand tiles, scales, work items
   DevBuf tc_runs, tc_jobs, tc_a, tc_sig, tc_parts, tc_items, tc_etab;
   // rotation-form free-space M2L: run info, operator jobs, batches, run starts
-  DevBuf rot_info, rot_jobs, rot_bat, rot_rs;
+  DevBuf rot_info, rot_jobs, rot_bat, rot_rs, rot_tab;
   DevBuf out_tmp;
   DevBuf cub_tmp;
 };

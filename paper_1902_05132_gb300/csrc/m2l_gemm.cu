@@ -340,13 +340,16 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
                  const int* vidx, BoxGeom B, const std::vector<CompGeom>& cgh, const cplx* Y, cplx* Z,
                  double* macs, cudaEvent_t ev_start, cudaStream_t st);
 
+void launch_l2l_rot(fmm_layered* h, const int* boxes, int n, BoxGeom B, const long* az_tab, cplx* L, cudaStream_t st);
+
 // Host driver: all V pairs of all levels.  L receives the M2L part for every
 // box with targets at level >= 2; then L2L level by level.
 void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector<int>>& m2l_lvl,
                   const int* dsched, const std::vector<long>& o_m2l, int maxlev, BoxGeom B, OpIndex OI,
                   const int* voff, const int* vidx, const cplx* free_ops, const cplx* reac_ops,
                   const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
-                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh) {
+                  cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh,
+                  const long* l2l_rot_tab) {
   Workspace& ws = h->ws;
   const int p = h->p, P = (p + 1) * (p + 1);
   const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;
@@ -481,9 +484,11 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     FMM_CHECK(cudaMemsetAsync(L, 0, sizeof(cplx) * (size_t)nb * P, st));
   }
   // L2L, top down
-  for (int l = 3; l <= maxlev; ++l)
-    if (!m2l_lvl[l].empty())
-      LAUNCH(k_l2l<<<(unsigned)m2l_lvl[l].size(), 128, sizeof(cplx) * P, st>>>(p, dsched + o_m2l[l], B, OI, l2l_ops, L));
+  for (int l = 3; l <= maxlev; ++l) {
+    if (m2l_lvl[l].empty()) continue;
+    if (l2l_rot_tab) launch_l2l_rot(h, dsched + o_m2l[l], (int)m2l_lvl[l].size(), B, l2l_rot_tab, L, st);
+    else LAUNCH(k_l2l<<<(unsigned)m2l_lvl[l].size(), 128, sizeof(cplx) * P, st>>>(p, dsched + o_m2l[l], B, OI, l2l_ops, L));
+  }
   FMM_CHECK(cudaGetLastError());
   (void)np;
 }

@@ -297,3 +297,188 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
   LAUNCH(k_zrot<<<(unsigned)bat.size(), 128, smem, st>>>(p, KC, db, R.w.as<cplx>(), R.az_buf.as<cplx>(), Y, Z));
   FMM_CHECK(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------- M2M and L2L in rotation form
+// The shifts between a box and its children factor the same way: with b the
+// child-minus-parent centre offset (direction (+-1, +-1, +-1)), M2M
+// conj(S^(b)) and L2L S^(b)^T equal W^T [operator at |b| z] conj(W), both
+// kinds of coefficients turning by conj(W) under the rotation.
+
+// one direction stage: out[i] = sum_j Wr(i, j) x[(n(i), j)] over the block of n(i)
+__device__ inline void rot_stage(int P, const cplx* Wc, const cplx* x, cplx* out, bool conj_rows, bool accumulate) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int n = deg_full(i), m = i - n * n - n, w2 = 2 * n + 1;
+    const cplx* xb = x + n * n;
+    cplx acc = accumulate ? out[i] : C(0, 0);
+    if (conj_rows) {
+      const cplx* wr = Wc + rot_ob(n) + (m + n) * w2;       // row (n, m) of conj(W)
+      for (int j = 0; j < w2; ++j) cfma(acc, cconj(wr[j]), xb[j]);
+    } else {
+      const cplx* wc = Wc + rot_ob(n) + (m + n);             // column (n, m) of W: W^T row
+      for (int j = 0; j < w2; ++j) cfma(acc, wc[j * w2], xb[j]);
+    }
+    out[i] = acc;
+  }
+}
+__device__ inline void coax_stage(int p, int P, const cplx* Az, const int* om, const cplx* x, cplx* out) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int n = deg_full(i), m = i - n * n - n, am = abs(m), nb = p + 1 - am;
+    const cplx* ar = Az + om[m + p] + (n - am) * nb;
+    cplx acc = C(0, 0);
+    for (int j = 0; j < nb; ++j) {
+      const int np_ = am + j;
+      cfma(acc, ar[j], x[np_ * np_ + np_ + m]);
+    }
+    out[i] = acc;
+  }
+}
+__device__ inline void load_coax(int p, int P, const cplx* A, const int* om, cplx* Az) {
+  for (int m = -p; m <= p; ++m) {
+    const int am = abs(m), nb = p + 1 - am, o = om[m + p];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int n = am + e / nb, np_ = am + e % nb;
+      Az[o + e] = A[(long)(np_ * np_ + np_ + m) * P + (n * n + n + m)];
+    }
+  }
+}
+__device__ inline int octant_slot(const int* coord) {
+  const int dx = (coord[0] & 1) ? 1 : -1, dy = (coord[1] & 1) ? 1 : -1, dz = (coord[2] & 1) ? 1 : -1;
+  return ((dz + 3) * 7 + (dy + 3)) * 7 + (dx + 3);
+}
+
+// M_b = sum over children with sources of the rotated shift of M_child (one CTA per parent box)
+__global__ void __launch_bounds__(128) k_m2m_rot(int p, const int* __restrict__ boxes, BoxGeom B,
+                                                 const long* __restrict__ az_tab, const cplx* __restrict__ Wall,
+                                                 const cplx* __restrict__ az_ops, cplx* __restrict__ M) {
+  const int b = boxes[blockIdx.x];
+  const int P = (p + 1) * (p + 1), NW = (int)rot_nw(p), NAZ = rot_naz(p);
+  extern __shared__ cplx sm[];
+  cplx* Wc = sm;
+  cplx* Az = Wc + NW;
+  cplx* x = Az + NAZ;
+  cplx* t = x + P;
+  cplx* acc = t + P;
+  __shared__ int om[2 * FMM_MAXP + 1];
+  for (int m = threadIdx.x - p; m <= p; m += blockDim.x) om[m + p] = rot_om(p, m);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) acc[i] = C(0, 0);
+  const int comp = B.comp[b];
+  bool az_loaded = false;
+  __syncthreads();
+  for (int k = 0; k < B.nchild[b]; ++k) {
+    const int c = B.child0[b] + k;
+    if (B.se[c] == B.sb[c]) continue;
+    if (!az_loaded) {                     // every child is one level below b
+      load_coax(p, P, az_ops + az_tab[comp * 23 + B.lev[c]], om, Az);
+      az_loaded = true;
+    }
+    const cplx* Wg = Wall + (long)octant_slot(B.coord + 3 * c) * NW;
+    for (int e = threadIdx.x; e < NW; e += blockDim.x) Wc[e] = Wg[e];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) x[i] = M[(long)c * P + i];
+    __syncthreads();
+    rot_stage(P, Wc, x, t, true, false);
+    __syncthreads();
+    coax_stage(p, P, Az, om, t, x);
+    __syncthreads();
+    rot_stage(P, Wc, x, acc, false, true);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < P; i += blockDim.x) M[(long)b * P + i] = acc[i];
+}
+
+// L_T += rotated shift of L_parent (one CTA per box of one level >= 3)
+__global__ void __launch_bounds__(128) k_l2l_rot(int p, const int* __restrict__ boxes, BoxGeom B,
+                                                 const long* __restrict__ az_tab, const cplx* __restrict__ Wall,
+                                                 const cplx* __restrict__ az_ops, cplx* __restrict__ L) {
+  const int T = boxes[blockIdx.x];
+  const int P = (p + 1) * (p + 1), NW = (int)rot_nw(p), NAZ = rot_naz(p);
+  extern __shared__ cplx sm[];
+  cplx* Wc = sm;
+  cplx* Az = Wc + NW;
+  cplx* x = Az + NAZ;
+  cplx* t = x + P;
+  cplx* out = t + P;
+  __shared__ int om[2 * FMM_MAXP + 1];
+  for (int m = threadIdx.x - p; m <= p; m += blockDim.x) om[m + p] = rot_om(p, m);
+  __syncthreads();
+  load_coax(p, P, az_ops + az_tab[B.comp[T] * 23 + B.lev[T]], om, Az);
+  const cplx* Wg = Wall + (long)octant_slot(B.coord + 3 * T) * NW;
+  for (int e = threadIdx.x; e < NW; e += blockDim.x) Wc[e] = Wg[e];
+  const int pa = B.parent[T];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    x[i] = L[(long)pa * P + i];
+    out[i] = L[(long)T * P + i];
+  }
+  __syncthreads();
+  rot_stage(P, Wc, x, t, true, false);
+  __syncthreads();
+  coax_stage(p, P, Az, om, t, x);
+  __syncthreads();
+  rot_stage(P, Wc, x, out, false, true);
+  __syncthreads();
+  for (int i = threadIdx.x; i < P; i += blockDim.x) L[(long)T * P + i] = out[i];
+}
+
+// Coaxial shift operators for every (component, level >= 3) present: table
+// of offsets into the rotation cache's operator buffer (-1 where unused).
+void rot_shift_tables(fmm_layered* h, const std::vector<CompGeom>& cgh, const std::vector<std::vector<char>>& has_level,
+                      int maxlev, std::vector<long>& m2m_az, std::vector<long>& l2l_az, cudaStream_t st) {
+  RotCache& R = h->rot;
+  const int p = h->p, P = (p + 1) * (p + 1), nc = (int)cgh.size();
+  rot_tables(h, st);
+  m2m_az.assign((size_t)nc * 23, -1);
+  l2l_az.assign((size_t)nc * 23, -1);
+  std::vector<SepJob> jobs;
+  for (int c = 0; c < nc; ++c)
+    for (int l = 3; l <= maxlev; ++l) {
+      if (!has_level[c][l]) continue;
+      const double w = cgh[c].h2 / (double)(1 << l);
+      for (int kind = 1; kind <= 2; ++kind) {
+        const double k = (kind == 1) ? cgh[c].ks : cgh[c].kt;
+        auto key = std::make_tuple(rbits(k), rbits(w), -kind);
+        auto it = R.az.find(key);
+        long off;
+        if (it == R.az.end()) {
+          off = R.az_used;
+          R.az_used += (long)P * P;
+          R.az[key] = off;
+          SepJob j{};
+          j.b[2] = 0.86602540378443864676 * w;      // |(+-w/2, +-w/2, +-w/2)|
+          j.k = k;
+          j.kind = kind;
+          j.out_off = off;
+          jobs.push_back(j);
+        } else {
+          off = it->second;
+        }
+        (kind == 1 ? m2m_az : l2l_az)[(size_t)c * 23 + l] = off;
+      }
+    }
+  if (!jobs.empty()) {
+    R.az_buf.grow_keep(sizeof(cplx) * (size_t)R.az_used, sizeof(cplx) * (size_t)(R.az_used - (long)jobs.size() * P * P),
+                       st);
+    SepJob* dj = (SepJob*)tc_need(h->ws.rot_jobs, sizeof(SepJob) * jobs.size() + 64);
+    FMM_CHECK(cudaMemcpyAsync(dj, jobs.data(), sizeof(SepJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+    launch_sep_ops(p, dj, (int)jobs.size(), h->tab.gaunt.as<double>(), R.az_buf.as<cplx>(), st);
+    FMM_CHECK(cudaGetLastError());
+    FMM_CHECK(cudaStreamSynchronize(st));   // the job table is rewritten by the next build
+  }
+}
+
+static size_t shift_smem(int p) {
+  const int P = (p + 1) * (p + 1);
+  return sizeof(cplx) * ((size_t)rot_nw(p) + rot_naz(p) + 3 * (size_t)P);
+}
+
+void launch_m2m_rot(fmm_layered* h, const int* boxes, int n, BoxGeom B, const long* az_tab, cplx* M, cudaStream_t st) {
+  if (!n) return;
+  const size_t smem = shift_smem(h->p);
+  FMM_CHECK(cudaFuncSetAttribute(k_m2m_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAUNCH(k_m2m_rot<<<n, 128, smem, st>>>(h->p, boxes, B, az_tab, h->rot.w.as<cplx>(), h->rot.az_buf.as<cplx>(), M));
+}
+
+void launch_l2l_rot(fmm_layered* h, const int* boxes, int n, BoxGeom B, const long* az_tab, cplx* L, cudaStream_t st) {
+  if (!n) return;
+  const size_t smem = shift_smem(h->p);
+  FMM_CHECK(cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LAUNCH(k_l2l_rot<<<n, 128, smem, st>>>(h->p, boxes, B, az_tab, h->rot.w.as<cplx>(), h->rot.az_buf.as<cplx>(), L));
+}
