@@ -83,6 +83,11 @@ __device__ inline unsigned long long morton3(unsigned ix, unsigned iy, unsigned 
 // ------------------------------------------------------------- classification
 // bbox layout: [set (0 src, 1 tgt)][layer][axis][min, max] (encoded doubles);
 // gap layout: [set][layer][side (0: z - d_l, 1: d_{l-1} - z)] (encoded).
+__global__ void k_iota(long n, int* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int)i;
+}
+
 __global__ void k_classify(long n, const double* __restrict__ xyz, const double* __restrict__ q, int set,
                            int L1, const double* __restrict__ d, unsigned char* __restrict__ layer,
                            unsigned* __restrict__ counts, unsigned long long* __restrict__ bbox,
@@ -499,9 +504,8 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     // iota values, radix sort on the layer byte (stable)
     int* iota = need<int>(ws.iota, std::max(ns, nt));
     unsigned char* ktmp = need<unsigned char>(ws.ltmp, std::max(ns, nt));
-    std::vector<int> hio(std::max(ns, nt));
-    for (long i = 0; i < (long)hio.size(); ++i) hio[i] = (int)i;
-    FMM_CHECK(cudaMemcpyAsync(iota, hio.data(), 4 * hio.size(), cudaMemcpyHostToDevice, st));
+    const long ni = std::max(ns, nt);
+    LAUNCH(k_iota<<<(unsigned)((ni + 255) / 256), 256, 0, st>>>(ni, iota));
     for (int set = 0; set < 2; ++set) {
       long n = set ? nt : ns;
       if (!n) continue;
