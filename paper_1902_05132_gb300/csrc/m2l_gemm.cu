@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "fmm_internal.h"
+#include "tiling.h"
 
 // owner[e] = target box of V-list entry e
 __global__ void k_v_owner(int nb, const int* __restrict__ voff, int* __restrict__ owner) {
@@ -123,8 +124,9 @@ struct GemmBatch {
 // One CTA per batch: the operator (R x C, input-major) stays in shared
 // memory; columns stream through in tiles of TK*KB.  Thread (tr, tk) owns rows
 // tr + TR*i (i < RPT) and columns tk + TK*j (j < KB).
-#define Z_RPT 3
-#define Z_KB 4
+#define Z_RPT 3                    // tiling::kRpt
+#define Z_KB 4                     // tiling::kKb
+static_assert(Z_RPT == tiling::kRpt && Z_KB == tiling::kKb, "tiling constants");
 __global__ void __launch_bounds__(128) k_zgemm_res(const GemmBatch* __restrict__ batches, const cplx* __restrict__ A,
                                                    const cplx* __restrict__ Y, cplx* __restrict__ Z) {
   const GemmBatch bt = batches[blockIdx.x];
@@ -292,42 +294,11 @@ __global__ void k_inverse_perm(long n, const int* __restrict__ perm, int* __rest
   if (k < n) inv[perm[k]] = (int)k;
 }
 
-// Shared memory of a CTA holding RB operator rows of a CB-wide contraction
-// chunk plus TK * Z_KB input columns of that chunk.
-static size_t gemm_smem(int RB, int CB, int TK) {
-  return sizeof(cplx) * ((size_t)RB * CB + (size_t)TK * Z_KB * CB);
-}
-static const size_t kGemmSmemCap = 200 * 1024;
-// Thread columns of a block of RB rows: as many as 128 threads allow, fewer
-// if the input tile would not fit beside the operator block.
-static int gemm_tk(int RB, int CB) {
-  int TK = 128 / ((RB + Z_RPT - 1) / Z_RPT);
-  while (TK > 1 && gemm_smem(RB, CB, TK) > kGemmSmemCap) --TK;
-  return TK;
-}
-// Tile of an R x R operator: the whole operator resident if it fits, else
-// row blocks of it (each resident), else 96-row blocks streamed in chunks
-// of the contraction.  Every block, the ragged last one included, fits.
-static void gemm_tiles(int R, int& RB, int& CB) {
-  auto full_tk = [](int rb) { return 128 / ((rb + Z_RPT - 1) / Z_RPT); };
-  RB = std::min(R, 3 * 128);
-  CB = R;
-  while (RB > 3 && gemm_smem(RB, CB, full_tk(RB)) > kGemmSmemCap) RB -= 3;
-  if (gemm_smem(RB, CB, full_tk(RB)) <= kGemmSmemCap) return;
-  RB = std::min(R, 96);
-  CB = (int)(kGemmSmemCap / gemm_smem(RB, 1, full_tk(RB)));
-}
-// Largest shared memory of any block of an R x R operator.
-static size_t gemm_smem_max(int R) {
-  int RB, CB;
-  gemm_tiles(R, RB, CB);
-  size_t m = 0;
-  for (int r0 = 0; r0 < R; r0 += RB) {
-    int rb = std::min(RB, R - r0);
-    m = std::max(m, gemm_smem(rb, CB, gemm_tk(rb, CB)));
-  }
-  return m;
-}
+using tiling::gemm_smem;
+using tiling::gemm_smem_max;
+using tiling::gemm_tiles;
+using tiling::gemm_tk;
+static_assert(sizeof(cplx) == tiling::kCplx, "complex layout");
 
 void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned long long>& hk,
                 const std::vector<int>& hc, const int* perm, const int* owner, const int* vidx, BoxGeom B,

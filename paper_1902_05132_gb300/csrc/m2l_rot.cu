@@ -21,14 +21,15 @@
 #include <vector>
 
 #include "fmm_internal.h"
+#include "tiling.h"
 
 void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st);
 
 namespace {
 
-__host__ __device__ inline long rot_nw(int p) { return (long)(p + 1) * (2 * p + 1) * (2 * p + 3) / 3; }
+using tiling::rot_naz;
+using tiling::rot_nw;
 __host__ __device__ inline int rot_ob(int n) { return n * (2 * n - 1) * (2 * n + 1) / 3; }   // start of block n
-__host__ __device__ inline int rot_naz(int p) { return (p + 1) * (2 * (p + 1) * (p + 1) + 1) / 3; }
 // start of the order-m block of the compact coaxial operator (m = -p..p)
 __host__ __device__ inline int rot_om(int p, int m) {
   int o = 0;
@@ -259,13 +260,7 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
     return off;
   };
   const int NW = (int)rot_nw(p), NAZ = rot_naz(p);
-  const size_t fixed = sizeof(cplx) * (size_t)(NW + NAZ);
-  // column tile: up to 32 columns within ~110 KB (two CTAs per SM) when at
-  // least 8 columns fit there, else within 200 KB
-  const size_t col_bytes = 2 * sizeof(cplx) * P;
-  int KC = (int)std::min<size_t>(32, (110 * 1024 - std::min<size_t>(fixed, 110 * 1024)) / col_bytes);
-  if (KC < 8) KC = (int)std::min<size_t>(32, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / col_bytes);
-  KC = std::max(KC, 1);
+  const int KC = tiling::rot_kc(p);            // column tile (tiling.h)
   std::vector<RotBatch> bat;
   for (size_t i = 0; i < runs.size(); ++i) {
     const int r = runs[i];
@@ -291,7 +286,7 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
   }
   RotBatch* db = (RotBatch*)tc_need(ws.rot_bat, sizeof(RotBatch) * bat.size() + 64);
   FMM_CHECK(cudaMemcpyAsync(db, bat.data(), sizeof(RotBatch) * bat.size(), cudaMemcpyHostToDevice, st));
-  const size_t smem = fixed + 2 * sizeof(cplx) * (size_t)KC * P;
+  const size_t smem = tiling::rot_smem(p);
   FMM_CHECK(cudaFuncSetAttribute(k_zrot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FMM_CHECK(cudaEventRecord(ev_start, st));   // the translation launches start here
   LAUNCH(k_zrot<<<(unsigned)bat.size(), 128, smem, st>>>(p, KC, db, R.w.as<cplx>(), R.az_buf.as<cplx>(), Y, Z));
@@ -464,21 +459,17 @@ void rot_shift_tables(fmm_layered* h, const std::vector<CompGeom>& cgh, const st
   }
 }
 
-static size_t shift_smem(int p) {
-  const int P = (p + 1) * (p + 1);
-  return sizeof(cplx) * ((size_t)rot_nw(p) + rot_naz(p) + 3 * (size_t)P);
-}
 
 void launch_m2m_rot(fmm_layered* h, const int* boxes, int n, BoxGeom B, const long* az_tab, cplx* M, cudaStream_t st) {
   if (!n) return;
-  const size_t smem = shift_smem(h->p);
+  const size_t smem = tiling::shift_smem(h->p);
   FMM_CHECK(cudaFuncSetAttribute(k_m2m_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LAUNCH(k_m2m_rot<<<n, 128, smem, st>>>(h->p, boxes, B, az_tab, h->rot.w.as<cplx>(), h->rot.az_buf.as<cplx>(), M));
 }
 
 void launch_l2l_rot(fmm_layered* h, const int* boxes, int n, BoxGeom B, const long* az_tab, cplx* L, cudaStream_t st) {
   if (!n) return;
-  const size_t smem = shift_smem(h->p);
+  const size_t smem = tiling::shift_smem(h->p);
   FMM_CHECK(cudaFuncSetAttribute(k_l2l_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LAUNCH(k_l2l_rot<<<n, 128, smem, st>>>(h->p, boxes, B, az_tab, h->rot.w.as<cplx>(), h->rot.az_buf.as<cplx>(), L));
 }

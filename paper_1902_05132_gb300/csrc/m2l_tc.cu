@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "fmm_internal.h"
+#include "tiling.h"
 
 namespace {
 
@@ -742,13 +743,10 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
   FMM_CHECK(cudaMemcpyAsync(ditems, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice, st));
   int max_np = 16;
   for (const TcItem& t : items) max_np = std::max(max_np, t.N_pad);
-  // two pipeline stages when two CTAs still fit on an SM; otherwise one
-  // stage, so that two CTAs share the SM and one's epilogue overlaps the
-  // other's copies and products (228 KB per SM, 1 KB reserved per CTA)
-  const size_t stage = 2 * (size_t)kTileM * kRowBytes + 2 * (size_t)max_np * kRowBytes;
-  const size_t per_sm = 228 * 1024;
-  const int nst = (2 * (2 * stage + 2048) <= per_sm) ? 2 : ((2 * (stage + 2048) <= per_sm) ? 1 : 2);
-  const size_t smem = 1024 + nst * stage;
+  // pipeline stages and shared memory (tiling.h): two stages when two CTAs
+  // still fit on an SM, otherwise one, so that two CTAs share the SM
+  const int nst = tiling::tc_stages(max_np);
+  const size_t smem = tiling::tc_smem(max_np);
   FMM_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FMM_CHECK(cudaEventRecord(gemm0, st));
   if (!items.empty())
