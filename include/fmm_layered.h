@@ -39,7 +39,9 @@ extern "C" {
 #define FMM_ERR_NONFINITE     -3   /* a coordinate or charge is NaN or Inf    */
 #define FMM_ERR_CUDA          -4   /* a CUDA call failed                      */
 #define FMM_ERR_OOM           -5   /* device allocation failed                */
-#define FMM_ERR_TIMEOUT       -6   /* reserved: bounded device wait expired   */
+#define FMM_ERR_TIMEOUT       -6   /* a bounded device wait expired (the kernel
+                                       released its resources; the context
+                                       stays usable)                          */
 #define FMM_ERR_UNSUPPORTED   -7   /* beyond the compiled limits              */
 
 /* flags for fmm_layered_create */
@@ -61,6 +63,17 @@ extern "C" {
                                  fmm_layered_direct come from the learned
                                  surrogate wherever its held-out check passed
                                  (quadrature elsewhere)                        */
+#define FMM_TREE_COUNTS  8u   /* reaction trees refined by the point counts
+                                 alone: without it a reaction-tree box that
+                                 touches the interface is refined while it
+                                 holds any point, which separates every
+                                 target leaf from every image leaf, so the
+                                 reaction components run entirely through
+                                 M2L.  With it, target leaves next to the
+                                 interface meet image leaves in their U, W
+                                 and X lists and those pairs are evaluated
+                                 directly (Sommerfeld quadrature of eq.
+                                 generalcomponentsimag, or the surrogate)    */
 #define FMM_TEST_STALL_TC (1u << 30) /* test only, with FMM_MIXED: every
                                  stage of the tensor-core M2L waits for 16
                                  bytes more than it copies, so its bounded
@@ -121,7 +134,8 @@ typedef struct {
  *               condition [eps du/dz] = 0 (host; NULL means all 1)
  *   p           expansion order, 1 <= p <= 16 (terms n = 0..p)
  *   leaf        maximum number of sources or targets in a leaf box, >= 1
- *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER | FMM_MIXED | FMM_SURROGATE
+ *   flags       FMM_PLAIN_FP64 | FMM_NORM_PAPER | FMM_MIXED | FMM_SURROGATE |
+ *               FMM_TREE_COUNTS
  *   out         receives the handle (NULL on failure)
  * Builds the contour quadrature rule and the reaction densities sigma at its
  * nodes on the current device.  Returns FMM_ERR_ARG for invalid input.

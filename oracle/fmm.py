@@ -20,13 +20,17 @@ Tree (reading c8 of the ambiguities; the paper leaves it to DASHMM):
   half (i_z >= 2^20 when targets lie above the interface) and images to the
   other half.  Stable sort by (key, original index), sources and targets
   separately.  A box at level l < 21 is refined iff it holds more than ``leaf``
-  sources or more than ``leaf`` targets, or -- in a reaction tree -- it touches
+  sources or more than ``leaf`` targets, or -- in a reaction tree, unless the
+  count-only rule is asked for (``split_interface=False``) -- it touches
   the interface (its closed z-extent contains the root's mid-plane) and holds
   any point; empty children are dropped.  The second rule separates every
   target leaf from every image leaf by at least one box, so the reaction
   components need no near-field evaluation as long as no point lies within
   2^-21 of the root width of the interface (design reading; the paper leaves
-  the refinement to DASHMM).  Boxes are numbered by (level, key prefix).
+  the refinement to DASHMM).  Under the count-only rule, target leaves next
+  to the interface have image leaves in their U, W and X lists, evaluated by
+  the Sommerfeld quadrature (the near field of Algorithm 1's last step).
+  Boxes are numbered by (level, key prefix).
 Lists (Cheng-Greengard-Rokhlin style, source boxes with >= 1 source, target
   boxes with >= 1 target; closed boxes touching = adjacent):
   V(T): children of the parent's colleagues not adjacent to T (M2L);
@@ -495,8 +499,10 @@ def components(medium, nsrc_layer, ntgt_layer):
     return out
 
 
-def component_tree(medium, comp, src, tgt, leaf):
-    """Root box, key clamps and tree of one component (src: images for reaction)."""
+def component_tree(medium, comp, src, tgt, leaf, split_interface=True):
+    """Root box, key clamps and tree of one component (src: images for
+    reaction); ``split_interface`` selects the interface rule of reaction
+    trees (see the module docstring)."""
     if comp.kind == "free":
         c, h = root_box(src, tgt)
         return Tree(src, tgt, leaf, c, h)
@@ -507,7 +513,7 @@ def component_tree(medium, comp, src, tgt, leaf):
         zt, zs = (half, 2 ** NBITS - 1), (0, half - 1)
     else:
         zt, zs = (0, half - 1), (half, 2 ** NBITS - 1)
-    return Tree(src, tgt, leaf, c, h, zclamp_src=zs, zclamp_tgt=zt, split_interface=True)
+    return Tree(src, tgt, leaf, c, h, zclamp_src=zs, zclamp_tgt=zt, split_interface=split_interface)
 
 
 # ============================================================== evaluation
@@ -516,12 +522,15 @@ class FMM:
 
     ``targets`` (optional) restricts the downward pass and the direct terms to
     a subset of target indices: every returned value is computed exactly as in
-    the full run (the full upward pass is always done)."""
+    the full run (the full upward pass is always done).
+    ``split_interface=False`` builds the reaction trees by the point counts
+    alone (count-only rule)."""
 
-    def __init__(self, medium, p, leaf):
+    def __init__(self, medium, p, leaf, split_interface=True):
         self.medium = medium
         self.p = int(p)
         self.leaf = int(leaf)
+        self.split_interface = bool(split_interface)
 
     def evaluate(self, src, q, tgt, targets=None, stats=None):
         med = self.medium
@@ -549,7 +558,7 @@ class FMM:
     # ------------------------------------------------------------------
     def _component(self, comp, spos, q, tpos, want, stats):
         med, p = self.medium, self.p
-        tree = component_tree(med, comp, spos, tpos, self.leaf)
+        tree = component_tree(med, comp, spos, tpos, self.leaf, self.split_interface)
         U, V, W, X = build_lists(tree)
         if stats is not None:
             stats.setdefault("components", []).append(

@@ -20,6 +20,7 @@ FMM_PLAIN_FP64 = 0
 FMM_NORM_PAPER = 1
 FMM_MIXED = 2
 FMM_SURROGATE = 4
+FMM_TREE_COUNTS = 8
 FMM_TEST_STALL_TC = 1 << 30
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "point on an interface", -3: "non-finite input",
@@ -148,10 +149,12 @@ class LayeredFMM:
     """Solver for one layered medium (Sec. 3.1): wave numbers k (top to bottom),
     interfaces d (descending), material coefficients eps, order p, leaf size.
     mixed=True runs the M2L translations on the tensor cores (FP16 hi/lo
-    operands, FP32 accumulation); every other stage stays FP64."""
+    operands, FP32 accumulation); every other stage stays FP64.
+    tree_counts=True refines reaction trees by the point counts alone
+    (FMM_TREE_COUNTS), so reaction components get near-field pairs."""
 
     def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False, mixed=False, surrogate=False,
-                 extra_flags=0):
+                 tree_counts=False, extra_flags=0):
         L = lib()
         self.k = np.ascontiguousarray(k, dtype=np.float64)
         self.d = np.ascontiguousarray(d, dtype=np.float64)
@@ -161,7 +164,8 @@ class LayeredFMM:
         rc = L.fmm_layered_create(len(self.k), _ptr(self.k), _ptr(self.d) if len(self.d) else None,
                                   _ptr(self.eps), self.p, self.leaf,
                                   (FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64) | (FMM_MIXED if mixed else 0)
-                                  | (FMM_SURROGATE if surrogate else 0) | int(extra_flags),
+                                  | (FMM_SURROGATE if surrogate else 0) | (FMM_TREE_COUNTS if tree_counts else 0)
+                                  | int(extra_flags),
                                   ctypes.byref(h))
         if rc != 0:
             raise FmmError(rc, L.fmm_layered_last_error(None).decode())

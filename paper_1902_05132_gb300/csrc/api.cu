@@ -231,7 +231,7 @@ extern "C" int fmm_layered_direct(fmm_layered_t* h, long ns, const double* src, 
         smin = fmin(smin, gap[(0 * h->L1 + l) * 2 + sd]);
         gmin = fmin(gmin, gap[(1 * h->L1 + l) * 2 + sd]);
       }
-    if (h->L1 > 1 && std::isfinite(gmin + smin)) rule_extend(h, h->rule.ta + 30.0 / (gmin + smin), st);
+    if (h->L1 > 1 && std::isfinite(gmin + smin)) rule_extend(h, h->rule.near_tmax(gmin + smin), st);
     cplx* coef = rule_coef(h, st);
     RuleView rv = make_rule_view(h->rule, coef);
     rv.surr = surrogate_view(h);
@@ -458,7 +458,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
       gmin = fmin(gmin, gap[(1 * h->L1 + l) * 2 + sd]);
     }
   if (h->L1 > 1 && std::isfinite(gmin + smin) && reac_near)
-    tmax = std::max(tmax, h->rule.ta + 30.0 / (gmin + smin));
+    tmax = std::max(tmax, h->rule.near_tmax(gmin + smin));
   if ((tmax - h->rule.ta) / h->rule.panel > 4.0e6)
     throw FmmError(FMM_ERR_UNSUPPORTED, "points too close to an interface: the quadrature tail would exceed 4e6 panels");
   rule_extend(h, tmax, st);

@@ -62,6 +62,33 @@ struct DevBuf {
 };
 
 enum { CK_FREE = 0, CK_REAC = 1 };
+
+// Reaction near-field integrals are taken on the real tail up to
+// ta + FMM_NEAR_TAIL_DECAY / H (H = vertical distance zt + zs of target and
+// image from the interface), where the integrand has decayed below e^{-30}.
+#define FMM_NEAR_TAIL_DECAY 30.0
+
+// Layer of a point of height z (the number of interfaces above it: layer l is
+// d_l < z < d_{l-1}), whether z lies exactly on an interface, and its
+// distances to the interface below (z - d_l) and above (d_{l-1} - z) within
+// its layer (INFINITY where the layer has none).  Shared by the
+// classification of the FMM and by the allocation-free direct sum.
+struct PointLayer {
+  int l;
+  bool on_iface;
+  double gap_below, gap_above;
+};
+__host__ __device__ inline PointLayer classify_height(double z, const double* d, int L1) {
+  PointLayer r{0, false, INFINITY, INFINITY};
+  for (int j = 0; j < L1 - 1; ++j) {
+    if (z == d[j]) r.on_iface = true;
+    if (z < d[j]) ++r.l;
+  }
+  if (r.l < L1 - 1) r.gap_below = z - d[r.l];
+  if (r.l > 0) r.gap_above = d[r.l - 1] - z;
+  return r;
+}
+
 enum { AR_UP = 0, AR_DOWN = 1 };
 
 // One FMM component (a free-space FMM of a layer or one reaction FMM).
@@ -88,6 +115,10 @@ struct Rule {
   int Q() const { return n_near + per_panel * n_tail_panels; }
   // number of nodes needed to integrate up to t_max on the tail
   int nodes_to(double tmax) const;
+  // does the rule reach t_max (no growth needed)?
+  bool covers(double tmax) const { return tmax <= ta + panel * n_tail_panels; }
+  // end of the tail needed by near-field pairs at vertical distance H
+  double near_tmax(double H) const { return ta + FMM_NEAR_TAIL_DECAY / H; }
 };
 
 struct Tables {             // expansion-order dependent tables built at create

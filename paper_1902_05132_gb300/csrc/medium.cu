@@ -248,8 +248,8 @@ void rule_init(fmm_layered* h) {
 
 void rule_extend(fmm_layered* h, double tmax, cudaStream_t st) {
   Rule& R = h->rule;
+  if (R.covers(tmax)) return;
   int need = (int)ceil((tmax - R.ta) / R.panel);
-  if (need <= R.n_tail_panels) return;
   need = need + need / 4 + 4;
   std::vector<cplx> kr, w;
   build_nodes(h, need, kr, w);

@@ -41,6 +41,7 @@ static void* scratch_address(int dev) {
 
 void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st);
 RuleView make_rule_view(const Rule& R, const cplx* coef);
+SurrView surrogate_view(const fmm_layered* h);
 void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
                    RuleView R, const cplx* coef_all, double* out, cudaStream_t st);
 void launch_norm_paper(long n, const double* tgt, DirectMedium md, double* out, cudaStream_t st);
@@ -63,14 +64,9 @@ __global__ void k_noalloc_scan(long n, const double* __restrict__ xyz, const dou
     atomicOr(flags, 2);
     return;
   }
-  int l = 0;
-  for (int j = 0; j < md.L1 - 1; ++j) {
-    if (z == md.d[j]) atomicOr(flags, 1);
-    if (z < md.d[j]) ++l;
-  }
-  double g = INFINITY;
-  if (l < md.L1 - 1) g = fmin(g, z - md.d[l]);
-  if (l > 0) g = fmin(g, md.d[l - 1] - z);
+  const PointLayer pl = classify_height(z, md.d, md.L1);
+  if (pl.on_iface) atomicOr(flags, 1);
+  const double g = fmin(pl.gap_below, pl.gap_above);
   if (isfinite(g)) atomicMin(&red[set], na_enc(g));
 }
 
@@ -126,15 +122,17 @@ extern "C" int fmm_layered_direct_noalloc(fmm_layered_t* h, long ns, const doubl
         return x;
       };
       double gsum = dec(hred[0]) + dec(hred[1]);
-      double need_t = R.ta + 30.0 / gsum;
-      double have_t = R.ta + R.panel * R.n_tail_panels;
-      if (need_t > have_t)
+      if (!R.covers(R.near_tmax(gsum)))
         throw FmmError(FMM_ERR_UNSUPPORTED,
                        "the quadrature rule held by the handle is too short for these points and growing it "
                        "would allocate: run fmm_layered_direct or fmm_layered_eval once on this geometry first");
     }
     launch_coef(h->L1, R, coef, st);
-    launch_direct(nt, tgt, ns, src, q, md, make_rule_view(R, coef), coef, out, st);
+    // the trained surrogate (FMM_SURROGATE) is read from the handle as in
+    // fmm_layered_direct: its weights and cell verdicts already exist
+    RuleView rv = make_rule_view(R, coef);
+    rv.surr = surrogate_view(h);
+    launch_direct(nt, tgt, ns, src, q, md, rv, coef, out, st);
     if (h->flags & FMM_NORM_PAPER) launch_norm_paper(nt, tgt, md, out, st);
     FMM_CHECK(cudaGetLastError());
     FMM_CHECK(cudaStreamSynchronize(st));

@@ -13,7 +13,6 @@
 
 #include "fmm_internal.h"
 
-#define TAIL_DECAY 30.0
 
 
 
@@ -35,7 +34,7 @@ __device__ inline cplx j0c(cplx z) {
 // One reaction pair on the rule (coef already holds sigma for the component).
 __device__ inline cplx reac_pair(const RuleView& R, const cplx* __restrict__ coef, const cplx* __restrict__ kzl,
                                  const cplx* __restrict__ kzp, double rho, double zt, double zs, int* nq_out = nullptr) {
-  int nq = rule_nodes(R, R.ta + TAIL_DECAY / (zt + zs));
+  int nq = rule_nodes(R, R.ta + FMM_NEAR_TAIL_DECAY / (zt + zs));
   if (nq_out) *nq_out = nq;
   cplx acc = C(0, 0);
   for (int q = 0; q < R.n_near; ++q) {

@@ -222,7 +222,7 @@ static void surr_train_impl(fmm_layered* h, double rho_max, double z_min, double
   const int nslot_all = L1 * L1 * 4;
   S.trained = false;
   // quadrature long enough for the smallest vertical distance zt + zs = 2 z_min
-  rule_extend(h, h->rule.ta + 30.0 / (2.0 * z_min), st);
+  rule_extend(h, h->rule.near_tmax(2.0 * z_min), st);
   const int Q = h->rule.Q();
   S.coef.ensure(sizeof(cplx) * (size_t)nslot_all * Q);
   launch_coef(L1, h->rule, S.coef.as<cplx>(), st);

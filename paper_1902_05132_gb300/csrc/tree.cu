@@ -26,7 +26,10 @@
 //    interface (the root's mid-plane) and holds any point; empty children are
 //    dropped.  The second rule keeps every target leaf at least one box away
 //    from every image leaf, so reaction components are evaluated entirely by
-//    M2L unless points lie within 2^-21 root widths of the interface.
+//    M2L unless points lie within 2^-21 root widths of the interface.  With
+//    FMM_TREE_COUNTS the second rule is off (refinement by the counts alone),
+//    and target leaves next to the interface meet image leaves in their U, W
+//    and X lists: the reaction near field of eq. generalcomponentsimag.
 //  * lists of a target box T (boxes with sources only, closed boxes touching
 //    = adjacent): V(T) children of the parent's colleagues not adjacent to T;
 //    for leaf T, U(T) source leaves adjacent to T (T included) and W(T)
@@ -102,11 +105,9 @@ __global__ void k_classify(long n, const double* __restrict__ xyz, const double*
     layer[i] = 0;
     return;
   }
-  int l = 0;
-  for (int j = 0; j < L1 - 1; ++j) {
-    if (z == d[j]) atomicOr(flags, FLAG_ON_INTERFACE);
-    if (z < d[j]) ++l;
-  }
+  const PointLayer pl = classify_height(z, d, L1);
+  if (pl.on_iface) atomicOr(flags, FLAG_ON_INTERFACE);
+  const int l = pl.l;
   layer[i] = (unsigned char)l;
   atomicAdd(&counts[set * L1 + l], 1u);
   double v[3] = {x, y, z};
@@ -117,8 +118,8 @@ __global__ void k_classify(long n, const double* __restrict__ xyz, const double*
     atomicMax(&bbox[base + 1], e);
   }
   size_t g = ((size_t)set * L1 + l) * 2;
-  if (l < L1 - 1) atomicMin(&gap[g], enc_double(z - d[l]));
-  if (l > 0) atomicMin(&gap[g + 1], enc_double(d[l - 1] - z));
+  if (l < L1 - 1) atomicMin(&gap[g], enc_double(pl.gap_below));
+  if (l > 0) atomicMin(&gap[g + 1], enc_double(pl.gap_above));
 }
 
 // ------------------------------------------------------------- gather
@@ -209,10 +210,10 @@ __device__ inline int lower_bound_u64(const unsigned long long* a, int lo, int h
   return lo;
 }
 
-__device__ inline bool refine_box(int level, int leaf, int ns, int nt, bool reac, int iz) {
+__device__ inline bool refine_box(int level, int leaf, int ns, int nt, bool split_iface, int iz) {
   if (level >= 21) return false;
   if (ns > leaf || nt > leaf) return true;
-  if (reac && ns + nt > 0) {
+  if (split_iface && ns + nt > 0) {
     if (level == 0) return true;
     int half = 1 << (level - 1);
     if (iz == half - 1 || iz == half) return true;
@@ -226,12 +227,12 @@ __global__ void k_count_children(int lb, int le, int level, int leaf, const int*
                                  const unsigned long long* __restrict__ skey,
                                  const unsigned long long* __restrict__ tkey, int* __restrict__ nchild,
                                  const int* __restrict__ comp, const int* __restrict__ comp_kind,
-                                 const int* __restrict__ coord) {
+                                 const int* __restrict__ coord, int split_iface) {
   int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= le) return;
   int ns = se[b] - sb[b], nt = te[b] - tb[b];
   int cnt = 0;
-  if (refine_box(level, leaf, ns, nt, comp_kind[comp[b]] == CK_REAC, coord[3 * b + 2])) {
+  if (refine_box(level, leaf, ns, nt, split_iface && comp_kind[comp[b]] == CK_REAC, coord[3 * b + 2])) {
     int shift = 3 * (21 - (level + 1));
     for (int o = 0; o < 8; ++o) {
       unsigned long long cp = (prefix[b] << 3) | o;
@@ -733,7 +734,8 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     int* scn = need<int>(ws.lvlscan, n + 1);
     LAUNCH(k_count_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, h->leaf, ws.bsb.as<int>(), ws.bse.as<int>(),
                                                       ws.btb.as<int>(), ws.bte.as<int>(), ws.bprefix.as<unsigned long long>(),
-                                                      skey, tkey, cntl, ws.bcomp.as<int>(), dkind, ws.bcoord.as<int>()));
+                                                      skey, tkey, cntl, ws.bcomp.as<int>(), dkind, ws.bcoord.as<int>(),
+                                                      (h->flags & FMM_TREE_COUNTS) ? 0 : 1));
     exclusive_scan(ws, cntl, scn, n, st);
     int last_cnt = 0, last_scan = 0;
     FMM_CHECK(cudaMemcpyAsync(&last_cnt, cntl + n - 1, 4, cudaMemcpyDeviceToHost, st));

@@ -155,11 +155,8 @@ def test_tree_invariants_and_list_completeness():
             assert tree.is_leaf[S] and (S == T or tree.adjacent(S, T))
 
 
-def test_reaction_tree_split_by_interface():
-    # Root box equally divided by the interface: every box of level >= 1 holds
-    # only targets or only images and its centre is on their side (eq.
-    # imagecentercond).
-    w = wl.three_layer(n=900, leaf=20)
+def _reaction_tree(split, n=900, leaf=20):
+    w = wl.three_layer(n=n, leaf=leaf)
     med = Medium(w["k"], w["d"], w["eps"])
     src, tgt = w["src"], w["tgt"]
     comp = fmm.Component("reac", 1, 2, DOWN, DOWN)
@@ -167,7 +164,48 @@ def test_reaction_tree_split_by_interface():
     img = src[ls == 2].copy()
     img[:, 2] = green.image_z(med, 1, 2, DOWN, DOWN, img[:, 2])
     t1 = tgt[ls == 1]
-    tree = fmm.component_tree(med, comp, img, t1, 20)
+    return med, fmm.component_tree(med, comp, img, t1, leaf, split_interface=split)
+
+
+def test_count_only_reaction_tree_lists_complete():
+    # Count-only refinement of a reaction tree: the root still splits targets
+    # from images at level 1 (eq. imagecentercond), every (target leaf, image)
+    # pair is accounted for by exactly one list, and some image leaves now sit
+    # in the U lists of target leaves (the reaction near field).
+    med, tree = _reaction_tree(False, n=1200, leaf=12)
+    dref = med.d[0]
+    for b in range(1, len(tree.level)):
+        cz = tree.center(b)[2]
+        if tree.ntgt[b]:
+            assert tree.nsrc[b] == 0 and cz < dref
+        if tree.nsrc[b]:
+            assert tree.ntgt[b] == 0 and cz > dref
+    U, V, W, X = fmm.build_lists(tree)
+    n_img = int(tree.nsrc[0])
+    n_near = 0
+    for T in np.nonzero(tree.is_leaf)[0]:
+        if tree.ntgt[T] == 0:
+            continue
+        cover = np.zeros(n_img, int)
+        for S in U.get(T, []) + W.get(T, []):
+            cover[tree.src_begin[S]:tree.src_end[S]] += 1
+            n_near += 1
+        for A in [T] + tree.ancestors(T):
+            for S in V.get(A, []) + X.get(A, []):
+                cover[tree.src_begin[S]:tree.src_end[S]] += 1
+        assert np.all(cover == 1), T
+    assert n_near > 0
+    # the interface rule leaves no near field on the same points
+    _, tree_i = _reaction_tree(True, n=1200, leaf=12)
+    Ui, _, Wi, Xi = fmm.build_lists(tree_i)
+    assert not Ui and not Wi and not Xi
+
+
+def test_reaction_tree_split_by_interface():
+    # Root box equally divided by the interface: every box of level >= 1 holds
+    # only targets or only images and its centre is on their side (eq.
+    # imagecentercond).
+    med, tree = _reaction_tree(True)
     dref = med.d[0]
     for b in range(1, len(tree.level)):
         cz = tree.center(b)[2]
@@ -211,9 +249,12 @@ def test_fmm_identical_layers_equals_free_space():
     assert np.linalg.norm(v - ref) / np.linalg.norm(ref) < 1e-5
 
 
-def test_fmm_equal_k_matches_images():
+@pytest.mark.parametrize("split", [True, False])
+def test_fmm_equal_k_matches_images(split):
     # Equal k, unequal eps, two layers: total field = free space + R x mirror
     # images in the source layer, (1 + R) x free space across (P2 at FMM level).
+    # With the count-only tree (split=False) the reaction components also
+    # take their near-field pairs by quadrature, checked here as well.
     rng = np.random.default_rng(8)
     n = 160
     src = rng.uniform(-1, 1, (n, 3))
@@ -223,7 +264,10 @@ def test_fmm_equal_k_matches_images():
     k, e0, e1 = 0.9, 1.0, 3.0
     med = Medium([k, k], [0.0], eps=[e0, e1])
     sel = np.arange(0, n, 9)
-    v = fmm.FMM(med, 9, 16).evaluate(src, q, src, targets=sel)
+    stats = {}
+    v = fmm.FMM(med, 9, 16, split_interface=split).evaluate(src, q, src, targets=sel, stats=stats)
+    n_reac_near = sum(c[3] for c in stats["components"] if c[0].startswith("reac"))
+    assert (n_reac_near > 0) == (not split), n_reac_near
     R01, R10 = (e0 - e1) / (e0 + e1), (e1 - e0) / (e0 + e1)
     ref = np.zeros(len(sel), complex)
     for n_, i in enumerate(sel):
