@@ -123,6 +123,8 @@ typedef struct {
                               the FP16 hi/lo tiles of the gathered columns
                               and of each operator used, read once, and the
                               FP64 translated columns written once           */
+  long   n_reac_surr_pairs;/* of n_reac_pairs, those the learned surrogate
+                              evaluated (FMM_SURROGATE)                      */
 } fmm_stats_t;
 
 /*
@@ -194,19 +196,23 @@ int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const long* n_src,
  * Learned surrogate of the reaction components (the form that replaces the
  * Sommerfeld quadrature of eq. generalcomponentsimag in the near field).
  * For every reaction component (l, l', a, b) of the medium, draws
- * samples_per_component points uniformly in the box rho in [0, rho_max],
- * zt, zs in [z_min, z_max] (zt: target distance to the component's reference
- * interface, zs: image depth) plus 1/8 as many held-out points (seeded
+ * samples_per_component points (rounded up to a multiple of 64) uniformly in
+ * the box rho in [0, rho_max], zt, zs in [z_min, z_max] (zt: target distance
+ * to the component's reference interface, zs: image depth), stratified over
+ * the cells of a 4 x 4 x 4 grid, plus 1/8 as many held-out points (seeded
  * counter-based generator), evaluates the component there with the
- * library's quadrature, and trains one MLP 3 -> 64 -> 64 -> 64 -> 2 (GELU;
- * BF16 weights and layer inputs, FP32 accumulation; Adam on FP32 master
- * weights; minibatch 1024, cosine learning-rate decay) for `steps` steps on
- * y = 4 pi R u, R = sqrt(rho^2 + (zt + zs)^2).  The held-out relative RMS
- * error is then measured on each cell of a 4 x 4 x 4 grid over the box; the
- * surrogate is used (with FMM_SURROGATE) only in cells within `bound`, and
- * the quadrature everywhere else and outside the box.  Retraining replaces the
- * previous networks.  Runs on `stream` and returns when done.
- * FMM_ERR_ARG for a single layer or invalid box/sizes.
+ * library's quadrature, and trains one network per component on
+ * y = 4 pi R u, R = sqrt(rho^2 + (zt + zs)^2): hidden layers 3 -> 64 -> 64 ->
+ * 64 (GELU) by Adam for `steps` steps on the standardized outputs (BF16
+ * weights and layer inputs, FP32 accumulation, FP32 master weights,
+ * minibatch 1024, cosine learning-rate decay), then a linear output layer
+ * 64 -> 2 per cell by least squares over the cell's samples (FP64 normal
+ * equations).  Inference carries weights and layer inputs as BF16 hi/lo
+ * pairs with FP32 accumulation.  The held-out relative RMS error is measured
+ * on each cell; the surrogate is used (with FMM_SURROGATE) only in cells
+ * within `bound`, and the quadrature everywhere else and outside the box.
+ * Retraining replaces the previous networks.  Runs on `stream` and returns
+ * when done.  FMM_ERR_ARG for a single layer or invalid box/sizes.
  */
 int fmm_layered_surrogate_train(fmm_layered_t* h, double rho_max, double z_min,
                                 double z_max, long samples_per_component,
@@ -223,6 +229,26 @@ int fmm_layered_surrogate_set_bound(fmm_layered_t* h, double bound);
  * 4 (L+1)^2 64 entries (host, either may be NULL).  FMM_ERR_ARG if untrained. */
 int fmm_layered_surrogate_report(const fmm_layered_t* h, double* cell_err,
                                  unsigned char* cell_ok);
+
+/*
+ * Gradient of the surrogate's training loss over one minibatch, computed by
+ * the training kernels of fmm_layered_surrogate_train (forward and backward
+ * with weights and layer inputs rounded to BF16, FP32 accumulation, the
+ * per-CTA partial gradients added in the order of the Adam step).  Exists to
+ * check those kernels against an independent implementation.
+ *   params  [FMM_SURR_NPARAM] FP32 parameters: W1 [64][3], b1 [64],
+ *           W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [2][64], b4 [2]
+ *           (row-major, output index first; host)
+ *   x       [1024][3] network inputs (host)
+ *   y       [1024][2] targets (host)
+ *   grad    [FMM_SURR_NPARAM] written: gradient of
+ *           (1/1024) sum_s |net(x_s) - y_s|^2 (host)
+ * Runs on the current device (allocates and frees its own buffers; legacy
+ * default stream, synchronous).  FMM_ERR_ARG for NULL pointers.
+ */
+#define FMM_SURR_NPARAM 8706
+#define FMM_SURR_BATCH 1024
+int fmm_layered_surrogate_grad(const float* params, const float* x, const float* y, float* grad);
 
 /* Same as fmm_layered_eval with HOST buffers: copies inputs to the device,
  * evaluates and copies the potentials back (all on `stream`). */

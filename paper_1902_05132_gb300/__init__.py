@@ -48,14 +48,16 @@ class Stats(ctypes.Structure):
                 ("n_free_ops", ctypes.c_long), ("n_reac_T_nodes", ctypes.c_long),
                 ("n_v_pairs_reac", ctypes.c_long), ("n_launches", ctypes.c_long),
                 ("gpu_ms_m2l_gemm", ctypes.c_double), ("m2l_gemm_flops", ctypes.c_double),
-                ("m2l_tensor_flops", ctypes.c_double), ("m2l_tc_bytes", ctypes.c_double)]
+                ("m2l_tensor_flops", ctypes.c_double), ("m2l_tc_bytes", ctypes.c_double),
+                ("n_reac_surr_pairs", ctypes.c_long)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
             "fmm_layered_eval_host", "fmm_layered_direct", "fmm_layered_stats",
             "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
             "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched",
-            "fmm_layered_surrogate_train", "fmm_layered_surrogate_report", "fmm_layered_surrogate_set_bound"]
+            "fmm_layered_surrogate_train", "fmm_layered_surrogate_report", "fmm_layered_surrogate_set_bound",
+            "fmm_layered_surrogate_grad"]
 
 _lib = None
 
@@ -89,6 +91,8 @@ def lib():
     L.fmm_layered_surrogate_set_bound.restype = i
     L.fmm_layered_surrogate_report.argtypes = [v, d, d]
     L.fmm_layered_surrogate_report.restype = i
+    L.fmm_layered_surrogate_grad.argtypes = [d, d, d, d]
+    L.fmm_layered_surrogate_grad.restype = i
     L.fmm_layered_stats.argtypes = [v, ctypes.POINTER(Stats)]
     L.fmm_layered_stats.restype = i
     L.fmm_layered_num_components.argtypes = [v]
@@ -288,6 +292,26 @@ class LayeredFMM:
             out.append(dict(kind=kind, l=l, lp=lp, a=a, b=b, ns=ns, nt=nt, root=root, prefix=prefix.view(np.uint64),
                             sperm=sperm[:ns], tperm=tperm[:nt], lists=lists, **arr))
         return out
+
+
+SURR_NPARAM = 8706
+SURR_BATCH = 1024
+
+
+def surrogate_grad(params, x, y):
+    """Gradient of the surrogate's training loss over one minibatch by the
+    library's training kernels (fmm_layered_surrogate_grad): params float32
+    [8706], x float32 [1024, 3], y float32 [1024, 2] (host arrays)."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    if params.shape != (SURR_NPARAM,) or x.shape != (SURR_BATCH, 3) or y.shape != (SURR_BATCH, 2):
+        raise ValueError("params [8706], x [1024, 3], y [1024, 2]")
+    g = np.zeros(SURR_NPARAM, dtype=np.float32)
+    rc = lib().fmm_layered_surrogate_grad(_ptr(params), _ptr(x), _ptr(y), _ptr(g))
+    if rc != 0:
+        raise FmmError(rc, "surrogate gradient failed")
+    return g
 
 
 def measure_fp64_peak():

@@ -624,8 +624,8 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   NB.uo = loff + (nb + 1); NB.ui = ws.ui.as<int>();
   NB.wo = loff + 2 * (nb + 1); NB.wi = ws.wi.as<int>();
   NB.xo = loff + 3 * (nb + 1); NB.xi = ws.xi.as<int>();
-  unsigned long long* counters = need<unsigned long long>(ws.iota, 4);
-  FMM_CHECK(cudaMemsetAsync(counters, 0, 32, st));
+  unsigned long long* counters = need<unsigned long long>(ws.iota, 6);
+  FMM_CHECK(cudaMemsetAsync(counters, 0, 48, st));
   launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st,
               (h->flags & FMM_MIXED) != 0);
@@ -633,7 +633,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   RuleView rv_reac = make_rule_view(h->rule, coef);
   rv_reac.surr = surrogate_view(h);
   launch_near(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, rv_reac,
-              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 2, st, false);
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 3, st, false);
   FMM_CHECK(cudaGetLastError());
   E.mark(7, st);
   for (int c = 0; c < nc; ++c)
@@ -642,9 +642,9 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaGetLastError());
   E.mark(8, st);
   int herr = 0;
-  unsigned long long hc[4];
+  unsigned long long hc[6];
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(hc, counters, 32, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(hc, counters, 48, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
   if (herr & 16) throw FmmError(FMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait on an mbarrier expired");
   if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair without an operator");
@@ -661,8 +661,9 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.gpu_ms_m2l_gemm = gemm_ran ? E.ms(10, 11) : 0.0;
   h->stats.m2l_gemm_flops = gemm_flops;
   h->stats.n_free_pairs = (long)hc[0];
-  h->stats.n_reac_pairs = (long)hc[2];
-  h->stats.n_reac_nodes = (long)hc[3];
+  h->stats.n_reac_pairs = (long)hc[3];
+  h->stats.n_reac_nodes = (long)hc[4];
+  h->stats.n_reac_surr_pairs = (long)hc[5];
   h->stats.n_launches = g_fmm_launches - launches0;
 }
 

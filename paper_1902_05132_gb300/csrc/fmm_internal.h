@@ -197,11 +197,12 @@ struct RotCache {
 struct SurrState {
   bool trained = false;
   double rho_max = 0, z_min = 0, z_max = 0, bound = 0;
-  DevBuf coef, slots, X, Y, Xh, Yh, wf, m, v, w16, gpart, acc, ok;
+  // winf: inference parameters [slot][2][SURR_NINF] (BF16 hi parts, then lo)
+  DevBuf coef, slots, X, Y, Xh, Yh, wf, m, v, winf, gpart, acc, ok, gram, musd;
   std::vector<double> cell_err;           // [slot][64] held-out relative RMS error, -1 if not judged
   std::vector<unsigned char> cell_ok;     // [slot][64] within the bound
   void release() {
-    DevBuf* all[] = {&coef, &slots, &X, &Y, &Xh, &Yh, &wf, &m, &v, &w16, &gpart, &acc, &ok};
+    DevBuf* all[] = {&coef, &slots, &X, &Y, &Xh, &Yh, &wf, &m, &v, &winf, &gpart, &acc, &ok, &gram, &musd};
     for (DevBuf* b : all) b->release();
   }
 };

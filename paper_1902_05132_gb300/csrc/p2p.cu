@@ -62,7 +62,7 @@ __device__ inline cplx reac_value(const RuleView& R, int slot, const cplx* __res
     float x[3];
     int cell;
     if (surr_inputs(R.surr, rho, zt, zs, x, &cell) && R.surr.ok[slot * SURR_CELLS + cell]) {
-      float2 y = surr_forward(R.surr.w + (long)slot * SURR_NPAR, x);
+      float2 y = surr_forward(R.surr.w + (long)slot * 2 * SURR_NINF, x, cell);
       double h = zt + zs;
       double f = 1.0 / (4.0 * FMM_PI * sqrt(rho * rho + h * h));
       if (nq_out) *nq_out = 0;
@@ -90,7 +90,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
                        RuleView R, const double* __restrict__ spos, const cplx* __restrict__ sq,
                        const double* __restrict__ tpos, cplx* __restrict__ phi,
                        unsigned long long* __restrict__ counters) {
-  unsigned long long my_pairs = 0, my_nodes = 0;
+  unsigned long long my_pairs = 0, my_nodes = 0, my_surr = 0;
   int T = leaves[blockIdx.x];
   const NearComp nc = ncs[B.comp[T]];
   __shared__ double sx[NEAR_CHUNK], sy[NEAR_CHUNK], sz[NEAR_CHUNK];
@@ -187,6 +187,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
               cfma(acc, reac_value(R, (int)(nc.coef_off / R.Q), coef, kzl, kzp, rho, zt, zs, &nq), sqs[kk]);
               ++my_pairs;
               my_nodes += nq;
+              my_surr += (nq == 0);
             }
           }
         }
@@ -201,6 +202,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
   if (counters && my_pairs) {
     atomicAdd(&counters[0], my_pairs);
     atomicAdd(&counters[1], my_nodes);
+    if (my_surr) atomicAdd(&counters[2], my_surr);
   }
 }
 
@@ -328,14 +330,19 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
 }
 
 // Training and held-out samples of the surrogate: points drawn uniformly in
-// the box by a counter-based generator, component values by the quadrature.
+// the box by a counter-based generator, stratified by cell (the samples of
+// component si and cell c are e = si nper + c (nper / 64) + j, j < nper / 64,
+// uniform within the cell), component values by the quadrature.
 __global__ void k_surr_samples(long n, long nper, const int* __restrict__ slots, int L1, SurrView box,
                                RuleView R, unsigned long long seed, float* __restrict__ X, float* __restrict__ Y) {
   long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int slot = slots[e / nper];
   const int lp = (slot >> 2) % L1, l = (slot >> 2) / L1;      // slot = ((l L1 + l') 2 + a) 2 + b
-  double u0 = surr_uniform(seed, 3 * e), u1 = surr_uniform(seed, 3 * e + 1), u2 = surr_uniform(seed, 3 * e + 2);
+  const int cell = (int)((e % nper) / (nper / SURR_CELLS));
+  const int c0 = cell >> 4, c1 = (cell >> 2) & 3, c2 = cell & 3;
+  double u0 = (c0 + surr_uniform(seed, 3 * e)) * 0.25, u1 = (c1 + surr_uniform(seed, 3 * e + 1)) * 0.25,
+         u2 = (c2 + surr_uniform(seed, 3 * e + 2)) * 0.25;
   double rho = u0 * box.rho_max;
   double zt = box.z_min + u1 * (box.z_max - box.z_min), zs = box.z_min + u2 * (box.z_max - box.z_min);
   cplx u = reac_pair(R, R.coef + (long)slot * R.Q, R.kz + (long)l * R.Q, R.kz + (long)lp * R.Q, rho, zt, zs);

@@ -6,10 +6,18 @@
 // interface of arrow a, zs the image depth of arrow b.  The network maps the
 // box-normalized inputs to y = 4 pi R u, R = sqrt(rho^2 + (zt + zs)^2) the
 // distance to the image point, which removes the 1/R decay and leaves an
-// O(1) smooth function.  Architecture: 3 -> 64 -> 64 -> 64 -> 2, GELU;
-// weights and layer inputs rounded to BF16, products accumulated in FP32.
-// The quadrature stays the reference: a held-out check per cell of a
-// 4 x 4 x 4 grid over the input box decides where the surrogate may be used.
+// O(1) smooth function.  Architecture: 3 -> 64 -> 64 -> 64 (GELU), then a
+// linear output layer 64 -> 2 (Re, Im) chosen by the cell of a 4 x 4 x 4 grid
+// over the input box.
+//  * Training: the three hidden layers and a shared output layer by Adam on
+//    the standardized outputs (weights and layer inputs rounded to BF16, FP32
+//    accumulation); then the output layer of every cell by ridge-regularized
+//    least squares (FP64 normal equations over that cell's training samples,
+//    features from the inference arithmetic below).
+//  * Inference: every weight and layer input carried as a BF16 hi/lo pair
+//    (x = hi + lo, a 16-bit significand), FP32 multiply-accumulate.
+// The quadrature stays the reference: a held-out check per cell decides where
+// the surrogate may be used.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -25,11 +33,18 @@
 #define SURR_B3 (SURR_W3 + SURR_H * SURR_H)
 #define SURR_W4 (SURR_B3 + SURR_H)
 #define SURR_B4 (SURR_W4 + 2 * SURR_H)
+// inference parameters of one component: the hidden layers (W1 .. b3), then
+// one output layer per cell, [cell][k][65] (64 weights and the bias of
+// output k); stored twice, BF16 hi parts then BF16 lo parts
+#define SURR_NTRUNK SURR_W4
+#define SURR_HEAD_N (SURR_H + 1)
+#define SURR_NHEAD (SURR_CELLS * 2 * SURR_HEAD_N)
+#define SURR_NINF (SURR_NTRUNK + SURR_NHEAD)
 
 // Box of the inputs and the trained networks (device pointers; w == nullptr:
 // no surrogate).
 struct SurrView {
-  const __nv_bfloat16* w;           // [slot][SURR_NPAR], slot = ((l L1 + l') 2 + a) 2 + b
+  const __nv_bfloat16* w;           // [slot][2][SURR_NINF], slot = ((l L1 + l') 2 + a) 2 + b
   const unsigned char* ok;          // [slot][SURR_CELLS]: held-out error within the bound
   double rho_max, z_min, z_max;
 };
@@ -65,36 +80,58 @@ __device__ inline bool surr_inputs(const SurrView& S, double rho, double zt, dou
   return true;
 }
 
-// Forward pass of one network for one input (BF16 weights from global memory,
-// FP32 accumulation, layer inputs rounded to BF16 as in training).
-__device__ inline float2 surr_forward(const __nv_bfloat16* __restrict__ W, const float* x) {
-  float a[SURR_H], b[SURR_H];
+// The value a BF16 hi/lo pair carries: hi = bf16(x), lo = bf16(x - hi).
+__device__ inline float surr_hilo(float x) {
+  float h = surr_bf(x);
+  return h + surr_bf(x - h);
+}
+__device__ inline float surr_w(const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo, int i) {
+  return __bfloat162float(hi[i]) + __bfloat162float(lo[i]);
+}
+
+// Hidden layers of one network for one input (inference arithmetic):
+// f[0..63] = GELU(W3 GELU(W2 GELU(W1 x + b1) + b2) + b3), every operand a
+// BF16 hi/lo pair, FP32 accumulation.  `hi` and `lo` point at the component's
+// inference parameters.
+__device__ inline void surr_features(const __nv_bfloat16* __restrict__ hi, const __nv_bfloat16* __restrict__ lo,
+                                     const float* x, float* f) {
+  float a[SURR_H];
+  float xi[3] = {surr_hilo(x[0]), surr_hilo(x[1]), surr_hilo(x[2])};
 #pragma unroll 4
   for (int j = 0; j < SURR_H; ++j) {
-    float s = __bfloat162float(W[SURR_B1 + j]);
-    for (int i = 0; i < 3; ++i) s = fmaf(__bfloat162float(W[SURR_W1 + j * 3 + i]), surr_bf(x[i]), s);
-    a[j] = surr_bf(surr_gelu(s));
+    float s = surr_w(hi, lo, SURR_B1 + j);
+    for (int i = 0; i < 3; ++i) s = fmaf(surr_w(hi, lo, SURR_W1 + j * 3 + i), xi[i], s);
+    a[j] = surr_hilo(surr_gelu(s));
   }
   for (int j = 0; j < SURR_H; ++j) {
-    float s = __bfloat162float(W[SURR_B2 + j]);
-    const __nv_bfloat16* wr = W + SURR_W2 + j * SURR_H;
+    float s = surr_w(hi, lo, SURR_B2 + j);
+    const int r = SURR_W2 + j * SURR_H;
 #pragma unroll 16
-    for (int i = 0; i < SURR_H; ++i) s = fmaf(__bfloat162float(wr[i]), a[i], s);
-    b[j] = surr_bf(surr_gelu(s));
+    for (int i = 0; i < SURR_H; ++i) s = fmaf(surr_w(hi, lo, r + i), a[i], s);
+    f[j] = surr_hilo(surr_gelu(s));
   }
   for (int j = 0; j < SURR_H; ++j) {
-    float s = __bfloat162float(W[SURR_B3 + j]);
-    const __nv_bfloat16* wr = W + SURR_W3 + j * SURR_H;
+    float s = surr_w(hi, lo, SURR_B3 + j);
+    const int r = SURR_W3 + j * SURR_H;
 #pragma unroll 16
-    for (int i = 0; i < SURR_H; ++i) s = fmaf(__bfloat162float(wr[i]), b[i], s);
-    a[j] = surr_bf(surr_gelu(s));
+    for (int i = 0; i < SURR_H; ++i) s = fmaf(surr_w(hi, lo, r + i), f[i], s);
+    a[j] = surr_hilo(surr_gelu(s));
   }
+  for (int j = 0; j < SURR_H; ++j) f[j] = a[j];
+}
+
+// Forward pass of one component's network for one input in `cell`.
+__device__ inline float2 surr_forward(const __nv_bfloat16* __restrict__ W, const float* x, int cell) {
+  const __nv_bfloat16* hi = W;
+  const __nv_bfloat16* lo = W + SURR_NINF;
+  float f[SURR_H];
+  surr_features(hi, lo, x, f);
   float o[2];
   for (int k = 0; k < 2; ++k) {
-    float s = __bfloat162float(W[SURR_B4 + k]);
-    const __nv_bfloat16* wr = W + SURR_W4 + k * SURR_H;
+    const int r = SURR_NTRUNK + (cell * 2 + k) * SURR_HEAD_N;
+    float s = surr_w(hi, lo, r + SURR_H);
 #pragma unroll 16
-    for (int i = 0; i < SURR_H; ++i) s = fmaf(__bfloat162float(wr[i]), a[i], s);
+    for (int i = 0; i < SURR_H; ++i) s = fmaf(surr_w(hi, lo, r + i), f[i], s);
     o[k] = s;
   }
   return make_float2(o[0], o[1]);

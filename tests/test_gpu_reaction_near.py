@@ -62,3 +62,40 @@ def test_reaction_near_field_fmm_matches_oracle_fmm():
     em = rel_l2(gm[sel], ref)
     print(f"mixed form, count-only trees: rel L2 vs oracle FMM {em:.2e}")
     assert em < 1e-5, em
+
+
+def test_surrogate_in_the_fmm_near_field():
+    # the same count-only FMM with the learned surrogate (FMM_SURROGATE):
+    # reaction near-field pairs whose cell passed the held-out check at 1e-5
+    # take the network, the others the quadrature.  Checked: the surrogate
+    # serves pairs, the potentials stay within the bound of the oracle FMM,
+    # and the reaction near field takes less device time than by quadrature.
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    w = _clustered()
+    src, q, tgt = to_dev(torch, w)
+    plain = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True)
+    surr = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True, surrogate=True)
+    err, ok = surr.train_surrogate(rho_max=2.9, z_min=0.09, z_max=1.11, samples=65536, steps=4000, bound=1e-5,
+                                   seed=3)
+    judged = err[err >= 0]
+    got_q = plain.eval(src, q, tgt).cpu().numpy()
+    plain.eval(src, q, tgt)
+    st_q = plain.stats()
+    got_s = surr.eval(src, q, tgt).cpu().numpy()
+    surr.eval(src, q, tgt)
+    st_s = surr.stats()
+    frac = st_s["n_reac_surr_pairs"] / st_s["n_reac_pairs"]
+    sel = workloads.sample_targets(len(w["tgt"]), 300, seed=4)
+    med = Medium(w["k"], w["d"], w["eps"])
+    ref = ofmm.FMM(med, w["p"], w["leaf"], split_interface=False).evaluate(w["src"], w["q"], w["tgt"], targets=sel)
+    e_s, e_q = rel_l2(got_s[sel], ref), rel_l2(got_q[sel], ref)
+    print(f"held-out error per cell: median {np.median(judged):.2e}, max {judged.max():.2e}, "
+          f"{int(ok.sum())} of {judged.size} cells within 1e-5; surrogate pairs {st_s['n_reac_surr_pairs']} of "
+          f"{st_s['n_reac_pairs']} ({100 * frac:.1f} %); reaction near field {st_s['gpu_ms_near_reac']:.3f} ms "
+          f"(quadrature {st_q['gpu_ms_near_reac']:.3f} ms); evaluation {st_s['gpu_ms_total']:.2f} ms "
+          f"(quadrature {st_q['gpu_ms_total']:.2f} ms); rel L2 vs oracle FMM {e_s:.2e} (quadrature {e_q:.2e})")
+    assert st_s["n_reac_surr_pairs"] > 0
+    assert e_s < 1e-5, e_s
+    if frac > 0.9:
+        assert st_s["gpu_ms_near_reac"] < st_q["gpu_ms_near_reac"]
