@@ -125,6 +125,13 @@ typedef struct {
                               FP64 translated columns written once           */
   long   n_reac_surr_pairs;/* of n_reac_pairs, those the learned surrogate
                               evaluated (FMM_SURROGATE)                      */
+  double reac_near_rho_max;/* the box of (rho, zt, zs) the reaction near-field
+                              pairs of the last evaluation needed: largest
+                              horizontal distance, smallest and largest
+                              distance of target or image to the interface
+                              (all 0 without reaction near-field pairs); the
+                              box to train the surrogate on                  */
+  double reac_near_z_min, reac_near_z_max;
 } fmm_stats_t;
 
 /*

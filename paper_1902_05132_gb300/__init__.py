@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
                 ("n_v_pairs_reac", ctypes.c_long), ("n_launches", ctypes.c_long),
                 ("gpu_ms_m2l_gemm", ctypes.c_double), ("m2l_gemm_flops", ctypes.c_double),
                 ("m2l_tensor_flops", ctypes.c_double), ("m2l_tc_bytes", ctypes.c_double),
-                ("n_reac_surr_pairs", ctypes.c_long)]
+                ("n_reac_surr_pairs", ctypes.c_long), ("reac_near_rho_max", ctypes.c_double),
+                ("reac_near_z_min", ctypes.c_double), ("reac_near_z_max", ctypes.c_double)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",

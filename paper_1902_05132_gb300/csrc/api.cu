@@ -37,6 +37,9 @@ void launch_l2p(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs,
                 const cplx* L, cplx* phi, cudaStream_t st);
 void launch_coef(int L1, const Rule& R, cplx* coef, cudaStream_t st);
 RuleView make_rule_view(const Rule& R, const cplx* coef);
+void launch_near_reac(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
+                      const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters,
+                      unsigned long long* box, cudaStream_t st);
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
                  const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st,
                  bool f32);
@@ -624,16 +627,19 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   NB.uo = loff + (nb + 1); NB.ui = ws.ui.as<int>();
   NB.wo = loff + 2 * (nb + 1); NB.wi = ws.wi.as<int>();
   NB.xo = loff + 3 * (nb + 1); NB.xi = ws.xi.as<int>();
-  unsigned long long* counters = need<unsigned long long>(ws.iota, 6);
-  FMM_CHECK(cudaMemsetAsync(counters, 0, 48, st));
+  // counters: free pairs, nodes, -, reaction pairs, nodes, surrogate pairs;
+  // then the reaction near-field box: max rho, min z, max z (double bits)
+  unsigned long long* counters = need<unsigned long long>(ws.iota, 9);
+  FMM_CHECK(cudaMemsetAsync(counters, 0, 72, st));
+  FMM_CHECK(cudaMemsetAsync(counters + 7, 0x7F, 8, st));      // min z starts above every finite value
   launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st,
               (h->flags & FMM_MIXED) != 0);
   E.mark(6, st);
   RuleView rv_reac = make_rule_view(h->rule, coef);
   rv_reac.surr = surrogate_view(h);
-  launch_near(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, rv_reac,
-              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 3, st, false);
+  launch_near_reac(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, rv_reac, ws.spos.as<double>(),
+                   ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 3, counters + 6, st);
   FMM_CHECK(cudaGetLastError());
   E.mark(7, st);
   for (int c = 0; c < nc; ++c)
@@ -642,9 +648,9 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaGetLastError());
   E.mark(8, st);
   int herr = 0;
-  unsigned long long hc[6];
+  unsigned long long hc[9];
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(hc, counters, 48, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(hc, counters, 72, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
   if (herr & 16) throw FmmError(FMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait on an mbarrier expired");
   if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair without an operator");
@@ -664,6 +670,14 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.n_reac_pairs = (long)hc[3];
   h->stats.n_reac_nodes = (long)hc[4];
   h->stats.n_reac_surr_pairs = (long)hc[5];
+  {
+    double bx[3];
+    memcpy(bx, hc + 6, sizeof(bx));
+    const bool any = hc[3] > 0;
+    h->stats.reac_near_rho_max = any ? bx[0] : 0.0;
+    h->stats.reac_near_z_min = any ? bx[1] : 0.0;
+    h->stats.reac_near_z_max = any ? bx[2] : 0.0;
+  }
   h->stats.n_launches = g_fmm_launches - launches0;
 }
 

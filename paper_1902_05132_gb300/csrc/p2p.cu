@@ -206,6 +206,138 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
   }
 }
 
+// Reaction components of the near field (U, W and X lists of reaction target
+// leaves; eq. generalcomponentsimag): one CTA per target leaf, one warp per
+// target (targets of the leaf strided over the warps).  The warp streams the
+// sources of the lists 32 at a time, one per lane.  Pairs whose cell the
+// surrogate covers are evaluated by their own lane (network forward pass);
+// the pairs left to the quadrature are then taken one at a time by the whole
+// warp, the lanes splitting the contour nodes (lane i takes nodes i, i + 32,
+// ...).  Every lane keeps a partial sum of q_s times its share; the partials
+// of a target are added by one warp-shuffle reduction in a fixed order.
+// box[0..2] (if given) receive max rho, min and max of zt and zs over the
+// pairs, as the bit patterns of non-negative doubles (ordered like the values).
+__device__ inline void warp_sum(cplx& v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leaves, NearBoxes B,
+                                                   const NearComp* __restrict__ ncs, RuleView R,
+                                                   const double* __restrict__ spos, const cplx* __restrict__ sq,
+                                                   const double* __restrict__ tpos, cplx* __restrict__ phi,
+                                                   unsigned long long* __restrict__ counters,
+                                                   unsigned long long* __restrict__ box) {
+  const int T = leaves[blockIdx.x];
+  const NearComp nc = ncs[B.comp[T]];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = (int)(nc.coef_off / R.Q);
+  const cplx* coef = R.coef + nc.coef_off;
+  const cplx* kzl = R.kz + (long)nc.l * R.Q;
+  const cplx* kzp = R.kz + (long)nc.lp * R.Q;
+  unsigned long long my_pairs = 0, my_nodes = 0, my_surr = 0;
+  double rho_hi = 0.0, z_lo = INFINITY, z_hi = 0.0;
+  for (int t = B.tb[T] + warp; t < B.te[T]; t += 4) {
+    const double x = tpos[3 * t], y = tpos[3 * t + 1];
+    const double zt = fabs(tpos[3 * t + 2] - nc.dref);
+    cplx acc = C(0, 0);
+    int A = T, phase = 0;                  // 0: U(T), 1: W(T), 2: X(A), A = T and its ancestors
+    int e = B.uo[T], e_end = B.uo[T + 1];
+    while (true) {
+      while (e >= e_end) {
+        if (phase == 0) { phase = 1; e = B.wo[T]; e_end = B.wo[T + 1]; }
+        else if (phase == 1) { phase = 2; A = T; e = B.xo[A]; e_end = B.xo[A + 1]; }
+        else {
+          A = B.parent[A];
+          if (A < 0) break;
+          e = B.xo[A]; e_end = B.xo[A + 1];
+        }
+      }
+      if (phase == 2 && A < 0) break;
+      const int S = (phase == 0) ? B.ui[e] : (phase == 1) ? B.wi[e] : B.xi[e];
+      ++e;
+      for (int s0 = B.sb[S]; s0 < B.se[S]; s0 += 32) {
+        const int s = s0 + lane;
+        const bool valid = s < B.se[S];
+        double rho = 0.0, zs = 1.0;
+        cplx qs = C(0, 0);
+        bool by_net = false;
+        if (valid) {
+          const double dx = x - spos[3 * s], dy = y - spos[3 * s + 1];
+          rho = sqrt(dx * dx + dy * dy);
+          zs = fabs(spos[3 * s + 2] - nc.dref);
+          qs = sq[s];
+          rho_hi = fmax(rho_hi, rho);
+          z_lo = fmin(z_lo, fmin(zt, zs));
+          z_hi = fmax(z_hi, fmax(zt, zs));
+          ++my_pairs;
+          if (R.surr.w) {
+            float xin[3];
+            int cell;
+            if (surr_inputs(R.surr, rho, zt, zs, xin, &cell) && R.surr.ok[slot * SURR_CELLS + cell]) {
+              const float2 v = surr_forward(R.surr.w + (long)slot * 2 * SURR_NINF, xin, cell);
+              const double f = 1.0 / (4.0 * FMM_PI * sqrt(rho * rho + (zt + zs) * (zt + zs)));
+              cfma(acc, C((double)v.x * f, (double)v.y * f), qs);
+              by_net = true;
+              ++my_surr;
+            }
+          }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, valid && !by_net);
+        while (todo) {
+          const int j = __ffs(todo) - 1;
+          todo &= todo - 1;
+          const double rj = __shfl_sync(0xffffffffu, rho, j), zsj = __shfl_sync(0xffffffffu, zs, j);
+          const cplx qj = C(__shfl_sync(0xffffffffu, qs.x, j), __shfl_sync(0xffffffffu, qs.y, j));
+          const int nq = rule_nodes(R, R.ta + FMM_NEAR_TAIL_DECAY / (zt + zsj));
+          cplx part = C(0, 0);
+          for (int qn = lane; qn < R.n_near; qn += 32) {
+            cplx ex = cexp_(cadd(cmul(C(0, zt), kzl[qn]), cmul(C(0, zsj), kzp[qn])));
+            cplx J = j0c(cscale(R.kr[qn], rj));
+            cfma(part, cmul(J, ex), coef[qn]);
+          }
+          double tail = 0.0;
+          for (int qn = R.n_near + lane; qn < nq; qn += 32) {
+            const double tq = R.kr[qn].x;
+            tail += coef[qn].x * j0(tq * rj) * exp(-(kzl[qn].y * zt + kzp[qn].y * zsj));
+          }
+          part.x += tail;
+          cfma(acc, part, qj);
+          if (lane == 0) my_nodes += nq;
+        }
+      }
+    }
+    warp_sum(acc);
+    if (lane == 0) phi[t] = cadd(phi[t], acc);
+  }
+  if (counters) {
+    for (int o = 16; o > 0; o >>= 1) {
+      my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, o);
+      my_surr += __shfl_xor_sync(0xffffffffu, my_surr, o);
+    }
+    if (lane == 0 && my_pairs) {
+      atomicAdd(&counters[0], my_pairs);
+      atomicAdd(&counters[1], my_nodes);
+      if (my_surr) atomicAdd(&counters[2], my_surr);
+    }
+  }
+  if (box) {
+    for (int o = 16; o > 0; o >>= 1) {
+      rho_hi = fmax(rho_hi, __shfl_xor_sync(0xffffffffu, rho_hi, o));
+      z_lo = fmin(z_lo, __shfl_xor_sync(0xffffffffu, z_lo, o));
+      z_hi = fmax(z_hi, __shfl_xor_sync(0xffffffffu, z_hi, o));
+    }
+    if (lane == 0 && z_hi > 0.0) {
+      atomicMax(&box[0], (unsigned long long)__double_as_longlong(rho_hi));
+      atomicMin(&box[1], (unsigned long long)__double_as_longlong(z_lo));
+      atomicMax(&box[2], (unsigned long long)__double_as_longlong(z_hi));
+    }
+  }
+}
+
 // All-pairs direct sum on the GPU: one thread per target, sources streamed
 // through shared memory.  Reaction part: all (a, b) of the layer pair.
 
@@ -357,6 +489,12 @@ __global__ void k_surr_samples(long n, long nper, const int* __restrict__ slots,
 void launch_surr_samples(long n, long nper, const int* slots, int L1, SurrView box, RuleView R,
                          unsigned long long seed, float* X, float* Y, cudaStream_t st) {
   if (n) LAUNCH(k_surr_samples<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, nper, slots, L1, box, R, seed, X, Y));
+}
+
+void launch_near_reac(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
+                      const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters,
+                      unsigned long long* box, cudaStream_t st) {
+  if (n) LAUNCH(k_near_reac<<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters, box));
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,

@@ -76,12 +76,15 @@ def test_surrogate_in_the_fmm_near_field():
     src, q, tgt = to_dev(torch, w)
     plain = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True)
     surr = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True, surrogate=True)
-    err, ok = surr.train_surrogate(rho_max=2.9, z_min=0.09, z_max=1.11, samples=65536, steps=4000, bound=1e-5,
-                                   seed=3)
-    judged = err[err >= 0]
     got_q = plain.eval(src, q, tgt).cpu().numpy()
     plain.eval(src, q, tgt)
     st_q = plain.stats()
+    # train on the box of (rho, zt, zs) this geometry's near field needs
+    box = dict(rho_max=1.001 * st_q["reac_near_rho_max"], z_min=0.999 * st_q["reac_near_z_min"],
+               z_max=1.001 * st_q["reac_near_z_max"])
+    assert 0 < box["z_min"] < box["z_max"] and box["rho_max"] > 0, box
+    err, ok = surr.train_surrogate(**box, samples=65536, steps=4000, bound=1e-5, seed=3)
+    judged = err[err >= 0]
     got_s = surr.eval(src, q, tgt).cpu().numpy()
     surr.eval(src, q, tgt)
     st_s = surr.stats()
@@ -90,7 +93,8 @@ def test_surrogate_in_the_fmm_near_field():
     med = Medium(w["k"], w["d"], w["eps"])
     ref = ofmm.FMM(med, w["p"], w["leaf"], split_interface=False).evaluate(w["src"], w["q"], w["tgt"], targets=sel)
     e_s, e_q = rel_l2(got_s[sel], ref), rel_l2(got_q[sel], ref)
-    print(f"held-out error per cell: median {np.median(judged):.2e}, max {judged.max():.2e}, "
+    print(f"near-field box rho <= {box['rho_max']:.3f}, z in [{box['z_min']:.3f}, {box['z_max']:.3f}]; "
+          f"held-out error per cell: median {np.median(judged):.2e}, max {judged.max():.2e}, "
           f"{int(ok.sum())} of {judged.size} cells within 1e-5; surrogate pairs {st_s['n_reac_surr_pairs']} of "
           f"{st_s['n_reac_pairs']} ({100 * frac:.1f} %); reaction near field {st_s['gpu_ms_near_reac']:.3f} ms "
           f"(quadrature {st_q['gpu_ms_near_reac']:.3f} ms); evaluation {st_s['gpu_ms_total']:.2f} ms "
