@@ -4,20 +4,35 @@ Default workload: the three-layer medium (interfaces z = 0, -1.2; k = 0.8,
 1.2, 1.6; eps = 1, 2, 3) with N = 32,768 particles split evenly over the cubes
 [-1,1]^2 x {[0.1,1.1], [-1.1,-0.1], [-2.3,-1.3]}, charges U[0,1], targets =
 sources, p = 8, leaf 64, FP64 throughout.  One step = one full evaluation
-(classification, trees, lists, translation operators, upward and downward
-passes, near field, sum), inputs resident in device memory.
+(classification, trees, lists, translation operators looked up in the
+handle's per-geometry cache, upward and downward passes, near field, sum),
+inputs resident in device memory.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-large] [--no-surrogate] [--no-cpu-baseline]
+
+Extra keys of the JSON line:
+  mixed      the same workload in the mixed-precision form (FMM_MIXED)
+  surrogate  count-only reaction trees (FMM_TREE_COUNTS), so that the
+             reaction components have a near field: FP64 with the quadrature
+             near field, then the mixed + surrogate form (FMM_MIXED |
+             FMM_SURROGATE) with the network trained on the near-field box
+  large      N = 2^20, p = 10, complex charges: FP64 and mixed forms
+  errors     each form against oracle values stored in
+             tests/golden/oracle_values_full.npz (written offline by
+             tests/golden/make_golden_full.py from the oracle alone)
 
 Multi-GPU (torchrun): every rank evaluates its own independent problem of the
 same size (weak scaling, no data-path collective); the barrier and the
 max-over-ranks time use torch.distributed.  --impl reference times the CPU
 oracle (the only reference implementation this project has) on a bounded
-sample of the same workload.
+sample of the same workload, on all host cores.
 """
 import argparse
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,12 +55,13 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["three-layer-32768"]
 METRIC = "FMM particles/sec at rel L2 err 1e-6 (FP64)"
 L2_BYTES = 129 * 1024 * 1024
-# DRAM bytes (read + write) of the M2L product launches of one evaluation of
-# the workload, from an ncu capture of the current kernel (None once the
-# kernel changes); the capture command is in the profile summary of the kernel.
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values_full.npz")
+# DRAM bytes (read + write) of the M2L product launches of one evaluation,
+# per (workload, form), from an ncu capture of the current kernels (absent once
+# a kernel changes); the capture command is in the kernel's profile summary.
 NCU_TRAFFIC = {
-    "three-layer N=32768 p=8 leaf=64": 94.521344e6 + 41.515520e6 + 806.672384e6 + 646.199040e6,
-    "mixed": 1260.710e6 + 755.058432e6,
+    ("three-layer N=32768 p=8 leaf=64", "fp64"): 94.521344e6 + 41.515520e6 + 806.672384e6 + 646.199040e6,
+    ("three-layer N=32768 p=8 leaf=64", "mixed"): 1260.710e6 + 755.058432e6,
 }
 
 
@@ -125,102 +141,237 @@ def _tensor_peak():
         return 1900.0, "fallback 1.9 PFLOP/s bf16 dense (of fallback)"
 
 
-def surrogate_leg(pkg, torch, w, dev, stream, n_targets=8192, n_sources=1024, samples=32768, steps=8000):
-    """Learned surrogate of the reaction components on the bench medium:
-    training time and held-out verdict, then the GPU direct sum at a sample
-    of targets (all sources) by quadrature and by the surrogate."""
-    s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], surrogate=True)
-    plain = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
-    t0 = time.perf_counter()
-    err, ok = s.train_surrogate(rho_max=2.9, z_min=0.09, z_max=1.11, samples=samples, steps=steps, bound=1e-5)
-    train_s = time.perf_counter() - t0
-    judged = err[err >= 0]
-    # the direct sum runs one thread per target: a wide target sample keeps the GPU busy
-    sel = np.linspace(0, len(w["tgt"]) - 1, n_targets).astype(np.int64)
-    ssel = np.linspace(0, len(w["src"]) - 1, n_sources).astype(np.int64)
-    src = torch.tensor(w["src"][ssel], device=dev)
-    q = torch.tensor(w["q"][ssel], device=dev)
-    tgt = torch.tensor(w["tgt"][sel], device=dev)
-    plain.direct(src, q, tgt)
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
-    def timed(solver):
+
+def _golden():
+    try:
+        return np.load(GOLDEN)
+    except OSError:
+        return None
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def timed_evals(torch, solver, src, q, tgt, out, steps, warmup, flush, stream):
+    """Warm-up, then `steps` evaluations each timed with CUDA events on the
+    evaluation stream, the L2 flushed before each; returns (ms list, stats)."""
+    for _ in range(max(3, warmup)):
+        solver.eval(src, q, tgt, out=out)
+    ms, stats = [], []
+    for _ in range(steps):
+        flush.fill_(1.0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        out = solver.direct(src, q, tgt)
+        solver.eval(src, q, tgt, out=out)
         e1.record(stream)
         e1.synchronize()
-        return out, e0.elapsed_time(e1)
-
-    ref, ms_q = timed(plain)
-    loose = 3e-2
-    _, ok_loose = s.surrogate_set_bound(loose)
-    s.direct(src, q, tgt)
-    got, ms_s = timed(s)
-    pairs = n_targets * n_sources
-    res = {
-        "components": int((err >= 0).any(axis=1).sum()), "samples_per_component": samples, "steps": steps,
-        "train_s": train_s, "heldout_rel_rms_median": float(np.median(judged)),
-        "heldout_rel_rms_max": float(judged.max()), "cells_within_1e-5": int(ok.sum()), "cells": int(judged.size),
-        "direct_sample": {"targets": n_targets, "sources": n_sources,
-                          "quadrature_pairs_per_s": pairs / (ms_q * 1e-3),
-                          "surrogate_bound": loose, "cells_used": int(ok_loose.sum()),
-                          "surrogate_pairs_per_s": pairs / (ms_s * 1e-3),
-                          "rel_l2_vs_quadrature": float(torch.linalg.vector_norm(got - ref) /
-                                                        torch.linalg.vector_norm(ref))},
-        "note": "the FMM near field of this workload has no reaction pairs (n_reac_pairs = 0), so the "
-                "mixed+surrogate evaluation equals the mixed one; the surrogate is measured on the direct sum",
-    }
-    s.close()
-    plain.close()
-    return res
+        ms.append(e0.elapsed_time(e1))
+        stats.append(solver.stats())
+    return ms, stats
 
 
-def cpu_oracle_sample(n_targets, seed=0):
-    """Time the oracle (as it stands: FP64 direct sum with Sommerfeld
-    quadrature) for n_targets sampled targets of the full workload against
-    all its sources, single-threaded, in a child process.  Returns targets
-    per second and the seconds taken."""
-    code = (
-        "import sys,time,json;sys.path.insert(0,%r);"
-        "from oracle.media import Medium;from oracle import green;"
-        "from paper_1902_05132_gb300 import workloads as wl;"
-        "w=wl.three_layer(n=%d,seed=%d,p=%d,leaf=%d,complex_charges=%s);m=Medium(w['k'],w['d'],w['eps']);"
-        "sel=wl.sample_targets(len(w['tgt']),%d,seed=3);t=time.perf_counter();"
-        "green.direct_sum(m,w['src'],w['q'],w['tgt'],targets=sel);"
-        "print(json.dumps({'seconds':time.perf_counter()-t}))"
-    ) % (ROOT, WORKLOAD["n"], seed, WORKLOAD["p"], WORKLOAD["leaf"], WORKLOAD["complex"], n_targets)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
-    return n_targets / sec, sec
+STAGES = ["tree", "operators", "upward", "m2l", "l2p", "near_free", "near_reac", "sum"]
+
+
+def _stage_ms(stats):
+    return {k: statistics.mean(s["gpu_ms_" + k] for s in stats) for k in STAGES}
+
+
+def _oracle_worker(args):
+    n, seed, p, leaf, complex_charges, idx = args
+    sys.path.insert(0, ROOT)
+    from oracle import green
+    from oracle.media import Medium
+    from paper_1902_05132_gb300 import workloads as wl
+    w = wl.three_layer(n=n, seed=seed, p=p, leaf=leaf, complex_charges=complex_charges)
+    m = Medium(w["k"], w["d"], w["eps"])
+    green.direct_sum(m, w["src"], w["q"], w["tgt"], targets=idx)
+    return len(idx)
+
+
+def cpu_oracle_sample(n_targets, cores=None, seed=0):
+    """Time the oracle as it stands (FP64 direct sum with Sommerfeld
+    quadrature) at n_targets sampled targets of the workload against all its
+    sources, the targets spread over `cores` worker processes (spawn, one
+    thread each).  Returns (targets per second, seconds, cores)."""
+    from paper_1902_05132_gb300 import workloads as wl
+    cores = cores or os.cpu_count() or 1
+    cores = max(1, min(cores, n_targets))
+    sel = wl.sample_targets(WORKLOAD["n"], n_targets, seed=3)
+    parts = [c for c in np.array_split(sel, cores) if len(c)]
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(parts)) as pool:
+        args = [(WORKLOAD["n"], seed, WORKLOAD["p"], WORKLOAD["leaf"], WORKLOAD["complex"], c) for c in parts]
+        empty = np.zeros(0, dtype=np.int64)                 # imports done in every worker before timing
+        pool.map(_oracle_worker, [a[:-1] + (empty,) for a in args], chunksize=1)
+        t = time.perf_counter()
+        done = sum(pool.map(_oracle_worker, args, chunksize=1))
+        sec = time.perf_counter() - t
+    return done / sec, sec, len(parts)
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    n_sample = max(1, 3 * 32768 // WORKLOAD["n"])
-    for _ in range(min(args.warmup, 1)):
-        cpu_oracle_sample(1)
+    cores = os.cpu_count() or 1
+    n_sample = max(cores, 2 * cores * 32768 // WORKLOAD["n"])
     vals, secs = [], []
+    used = 1
     for _ in range(args.steps):
-        v, s = cpu_oracle_sample(n_sample)
+        v, s, used = cpu_oracle_sample(n_sample, cores)
         vals.append(v)
         secs.append(s)
     value = statistics.median(vals)
     sample = (f"oracle direct sum (FP64, Sommerfeld quadrature) at {n_sample} sampled targets of the "
-              f"{WORKLOAD['name']} workload against all its sources, per step")
+              f"{WORKLOAD['name']} workload against all its sources per step, spread over {used} worker processes "
+              f"on {cores} host cores ({_cpu_model()})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "sample_targets": n_sample},
-        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def mixed_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws):
+    """The mixed-precision form on the same workload: throughput, error
+    against the FP64 path, roofline of the tensor-core M2L product."""
+    n = len(w["tgt"])
+    mixed = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], mixed=True)
+    out_m = torch.empty_like(ref_out)
+    torch.cuda.nvtx.range_push("timed_mixed")
+    mms, mst = timed_evals(torch, mixed, src, q, tgt, out_m, args.steps, args.warmup, flush, stream)
+    torch.cuda.nvtx.range_pop()
+    mixed.close()
+    m_ms = statistics.mean(mms)
+    tc_ms = statistics.mean(s["gpu_ms_m2l_gemm"] for s in mst)
+    tc_flops = mst[-1]["m2l_tensor_flops"]
+    bf16_peak, peak_src = _tensor_peak()
+    tc_achieved = tc_flops / (tc_ms * 1e-3) / 1e12
+    tc_bytes = mst[-1]["m2l_tc_bytes"]
+    tc_gbs = tc_bytes / (tc_ms * 1e-3) / 1e9
+    hbm_peak, hbm_src = _hbm_peak()
+    res = {
+        "value": ws * n / (m_ms * 1e-3), "unit": "particles/s", "ms_per_step": m_ms,
+        "rel_l2_vs_fp64_path": float(torch.linalg.vector_norm(out_m - ref_out) / torch.linalg.vector_norm(ref_out)),
+        "dtype": "f16 hi/lo -> f32 (M2L), f64 elsewhere", "stage_ms": _stage_ms(mst),
+        # the product moves ~70 flop per byte, below the FP16 tensor balance
+        # point (peak flops / HBM bandwidth ~ 280): it is bounded by HBM
+        "roofline": {"bound": "hbm", "kernel": "k_m2l_tc", "achieved": tc_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": tc_gbs / hbm_peak, "traffic": NCU_TRAFFIC.get((w["name"], "mixed")),
+                     "kernel_ms": tc_ms, "algorithmic_gb": tc_bytes / 1e9, "peak_source": hbm_src,
+                     "tensor": {"achieved": tc_achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                                "frac": tc_achieved / bf16_peak, "executed_tflop": tc_flops / 1e12,
+                                "peak_source": peak_src},
+                     "algorithmic_fp64_equiv_tflop": mst[-1]["m2l_gemm_flops"] / 1e12},
+    }
+    return res, out_m
+
+
+def surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, gold):
+    """Count-only reaction trees (FMM_TREE_COUNTS): the reaction components
+    get a near field.  FP64 with the quadrature there (the method without
+    the network), then the surrogate trained on the (rho, zt, zs) box that
+    near field needs, and the mixed + surrogate form timed on the same trees."""
+    n = len(w["tgt"])
+    out = torch.empty_like(ref_out)
+    plain = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True)
+    qms, qst = timed_evals(torch, plain, src, q, tgt, out, max(1, args.steps // 2), 1, flush, stream)
+    out_q = out.clone()
+    plain.close()
+    st_q = qst[-1]
+    box = dict(rho_max=1.001 * st_q["reac_near_rho_max"], z_min=0.999 * st_q["reac_near_z_min"],
+               z_max=1.001 * st_q["reac_near_z_max"])
+    ms_surr = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True, mixed=True,
+                             surrogate=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    err, ok = ms_surr.train_surrogate(**box, samples=131072, steps=8000, bound=1e-5, seed=5)
+    train_s = time.perf_counter() - t0
+    judged = err[err >= 0]
+    torch.cuda.nvtx.range_push("timed_mixed_surrogate")
+    sms, sst = timed_evals(torch, ms_surr, src, q, tgt, out, args.steps, args.warmup, flush, stream)
+    torch.cuda.nvtx.range_pop()
+    ms_surr.close()
+    st_s = sst[-1]
+    res = {
+        "trees": "count-only reaction trees (FMM_TREE_COUNTS)",
+        "fp64_quadrature": {"value": ws * n / (statistics.mean(qms) * 1e-3), "ms_per_step": statistics.mean(qms),
+                            "near_reac_ms": statistics.mean(s["gpu_ms_near_reac"] for s in qst),
+                            "n_reac_pairs": st_q["n_reac_pairs"], "n_reac_nodes": st_q["n_reac_nodes"],
+                            "rel_l2_vs_fp64_path": _rel(out_q.cpu().numpy(), ref_out.cpu().numpy())},
+        "training": {"box": box, "samples_per_component": 131072, "steps": 8000, "train_s": train_s,
+                     "components": int((err >= 0).any(axis=1).sum()),
+                     "heldout_rel_rms_median": float(np.median(judged)), "heldout_rel_rms_max": float(judged.max()),
+                     "cells_within_1e-5": int(ok.sum()), "cells": int(judged.size)},
+        "mixed_surrogate": {"value": ws * n / (statistics.mean(sms) * 1e-3), "unit": "particles/s",
+                            "ms_per_step": statistics.mean(sms), "stage_ms": _stage_ms(sst),
+                            "surrogate_pairs": st_s["n_reac_surr_pairs"], "reac_pairs": st_s["n_reac_pairs"],
+                            "surrogate_fraction": st_s["n_reac_surr_pairs"] / max(1, st_s["n_reac_pairs"]),
+                            "rel_l2_vs_fp64_path": _rel(out.cpu().numpy(), ref_out.cpu().numpy())},
+    }
+    if gold is not None:
+        sel = gold["three_layer_sel2000"]
+        res["mixed_surrogate"]["rel_l2_vs_oracle_direct_2000"] = _rel(out.cpu().numpy()[sel],
+                                                                      gold["three_layer_direct2000"])
+        res["fp64_quadrature"]["rel_l2_vs_oracle_direct_2000"] = _rel(out_q.cpu().numpy()[sel],
+                                                                      gold["three_layer_direct2000"])
+    return res
+
+
+def large_leg(pkg, torch, dev, args, flush, stream, gold):
+    """N = 2^20, p = 10, complex charges: FP64 and mixed forms, each against
+    the oracle direct sum at the stored sampled targets."""
+    from paper_1902_05132_gb300 import workloads
+    spec = WORKLOADS["three-layer-1M"]
+    w = workloads.three_layer(n=spec["n"], p=spec["p"], leaf=spec["leaf"], complex_charges=True)
+    src = torch.tensor(w["src"], device=dev)
+    q = torch.tensor(w["q"], device=dev)
+    tgt = torch.tensor(w["tgt"], device=dev)
+    n = len(w["tgt"])
+    res = {"workload": spec["name"]}
+    outs = {}
+    for form, kw in (("fp64", {}), ("mixed", {"mixed": True})):
+        s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], **kw)
+        out = torch.empty(n, dtype=torch.complex128, device=dev)
+        ms, st = timed_evals(torch, s, src, q, tgt, out, max(2, args.steps // 2), 3, flush, stream)
+        s.close()
+        r = {"value": n / (statistics.mean(ms) * 1e-3), "unit": "particles/s", "ms_per_step": statistics.mean(ms),
+             "stage_ms": _stage_ms(st), "m2l_kernel_ms": statistics.mean(x["gpu_ms_m2l_gemm"] for x in st)}
+        if form == "fp64":
+            peak = pkg.measure_fp64_peak() / 1e3
+            ach = st[-1]["m2l_gemm_flops"] / (r["m2l_kernel_ms"] * 1e-3) / 1e12
+            r["roofline"] = {"bound": "alu", "kernel": "k_zrot + k_zgemm_res", "achieved": ach, "peak": peak,
+                             "unit": "TFLOP/s", "frac": ach / peak, "traffic": None}
+        else:
+            hbm, _ = _hbm_peak()
+            gbs = st[-1]["m2l_tc_bytes"] / (r["m2l_kernel_ms"] * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "kernel": "k_m2l_tc", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                             "frac": gbs / hbm, "traffic": None}
+        outs[form] = out.cpu().numpy()
+        if gold is not None:
+            sel = gold["three_layer_1m_sel"]
+            r["rel_l2_vs_oracle_direct"] = _rel(outs[form][sel], gold["three_layer_1m_direct"])
+            r["oracle_targets"] = int(len(sel))
+        res[form] = r
+    res["mixed"]["rel_l2_vs_fp64_path"] = _rel(outs["mixed"], outs["fp64"])
+    return res
 
 
 def main():
@@ -231,6 +382,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--workload", default="three-layer-32768", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     global WORKLOAD
@@ -306,7 +458,8 @@ def main():
     c1.synchronize()
     cst = cold.stats()
     cold_info = {"ms": c0.elapsed_time(c1), "operators_ms": cst["gpu_ms_operators"],
-                 "reaction_classes": cst["n_reac_classes"], "free_operators": cst["n_free_ops"]}
+                 "reaction_classes": cst["n_reac_classes"], "free_operators": cst["n_free_ops"],
+                 "particles_per_s": n / (c0.elapsed_time(c1) * 1e-3)}
     cold.close()
 
     # end to end through the public API with host buffers (pinned)
@@ -325,89 +478,61 @@ def main():
     h2d = hs.nbytes + hq.nbytes + ht.nbytes
     d2h = res.nbytes
 
-    # roofline of the dominant stage (FP64 pipe, peak measured on this GPU now)
-    keys = ["tree", "operators", "upward", "m2l", "l2p", "near_free", "near_reac", "sum"]
-    mean_stage = {k: statistics.mean(s["gpu_ms_" + k] for s in stage) for k in keys}
-    # dominant kernels: the M2L translations (k_zrot for free-space classes in
-    # rotation form, k_zgemm_res for reaction classes), timed by the library's
-    # CUDA events around their launches on the evaluation's stream
+    # roofline of the dominant kernels: the M2L translations (k_zrot for
+    # free-space classes in rotation form, k_zgemm_res for reaction classes),
+    # timed by the library's CUDA events around their launches on the
+    # evaluation's stream; FP64 pipe peak measured on this GPU now
     gemm_ms = statistics.mean(s["gpu_ms_m2l_gemm"] for s in stage)
     gemm_flops = stage[-1]["m2l_gemm_flops"]
     peak = pkg.measure_fp64_peak() / 1e3
     achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC.get(WORKLOAD["name"])
     result = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "medium": "3 layers, d=(0,-1.2), k=(0.8,1.2,1.6), eps=(1,2,3)",
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"independent problem per GPU x{ws}"},
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"independent problem per GPU x{ws}",
+                   "operators": "translation operators cached in the handle per geometry (warm); a new geometry "
+                                "pays cold_first_eval"},
         "clocks": _clock_summary(clock_path),
         "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_zrot + k_zgemm_res", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((WORKLOAD["name"], "fp64")),
                      "per": "the M2L translation launches of one evaluation (free-space and reaction classes)",
                      "kernel_ms": gemm_ms, "algorithmic_tflop": gemm_flops / 1e12,
                      "peak_source": "FP64 FMA throughput measured on this GPU by the library's probe (of measured)"},
-        "stage_ms": mean_stage,
+        "stage_ms": _stage_ms(stage),
         "cold_first_eval": cold_info,
         "counts": {k: stage[-1][k] for k in ("n_components", "n_boxes", "n_v_pairs", "n_v_pairs_reac", "n_free_pairs",
                                              "n_reac_pairs", "n_reac_nodes", "n_reac_classes", "n_reac_T_nodes")},
     }
-    # mixed-precision form on the same workload: M2L on the tensor cores
+    gold = _golden() if WORKLOAD["n"] == 32768 and not WORKLOAD["complex"] and rank == 0 else None
     ref_out = out.clone()
-    mixed = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], mixed=True)
-    out_m = torch.empty_like(out)
-    for _ in range(max(3, args.warmup)):
-        mixed.eval(src, q, tgt, out=out_m)
-    mms, mst = [], []
-    torch.cuda.nvtx.range_push("timed_mixed")
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mixed.eval(src, q, tgt, out=out_m)
-        e1.record(stream)
-        e1.synchronize()
-        mms.append(e0.elapsed_time(e1))
-        mst.append(mixed.stats())
-    torch.cuda.nvtx.range_pop()
-    m_ms = statistics.mean(mms)
-    tc_ms = statistics.mean(s["gpu_ms_m2l_gemm"] for s in mst)
-    tc_flops = mst[-1]["m2l_tensor_flops"]
-    bf16_peak, peak_src = _tensor_peak()
-    tc_achieved = tc_flops / (tc_ms * 1e-3) / 1e12
-    tc_bytes = mst[-1]["m2l_tc_bytes"]
-    tc_gbs = tc_bytes / (tc_ms * 1e-3) / 1e9
-    hbm_peak, hbm_src = _hbm_peak()
-    err_m = float(torch.linalg.vector_norm(out_m - ref_out) / torch.linalg.vector_norm(ref_out))
-    result["mixed"] = {
-        "value": ws * n / (m_ms * 1e-3), "unit": "particles/s", "ms_per_step": m_ms,
-        "rel_l2_vs_fp64_path": err_m, "dtype": "f16 hi/lo -> f32 (M2L), f64 elsewhere",
-        "stage_ms": {k: statistics.mean(s["gpu_ms_" + k] for s in mst) for k in keys},
-        # the product moves ~70 flop per byte, below the FP16 tensor balance
-        # point (peak flops / HBM bandwidth ~ 280): it is bounded by HBM
-        "roofline": {"bound": "hbm", "kernel": "k_m2l_tc", "achieved": tc_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": tc_gbs / hbm_peak, "traffic": NCU_TRAFFIC.get("mixed"),
-                     "kernel_ms": tc_ms, "algorithmic_gb": tc_bytes / 1e9,
-                     "peak_source": hbm_src,
-                     "tensor": {"achieved": tc_achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                                "frac": tc_achieved / bf16_peak, "executed_tflop": tc_flops / 1e12,
-                                "peak_source": peak_src},
-                     "algorithmic_fp64_equiv_tflop": mst[-1]["m2l_gemm_flops"] / 1e12},
-    }
-    mixed.close()
+    if gold is not None:
+        sel = gold["three_layer_sel2000"]
+        result["errors"] = {"fp64_vs_oracle_direct_2000": _rel(ref_out.cpu().numpy()[sel],
+                                                               gold["three_layer_direct2000"]),
+                            "fp64_vs_oracle_fmm_200": _rel(ref_out.cpu().numpy()[gold["three_layer_fmm_sel"]],
+                                                           gold["three_layer_fmm200"])}
+    result["mixed"], out_m = mixed_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws)
+    if gold is not None:
+        result["errors"]["mixed_vs_oracle_direct_2000"] = _rel(out_m.cpu().numpy()[gold["three_layer_sel2000"]],
+                                                               gold["three_layer_direct2000"])
     if not args.no_surrogate:
-        result["surrogate"] = surrogate_leg(pkg, torch, w, dev, stream)
+        result["surrogate"] = surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, gold)
+    if not args.no_large and ws == 1:
+        result["large"] = large_leg(pkg, torch, dev, args, flush, stream, _golden())
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        n_sample = max(1, 6 * 32768 // WORKLOAD["n"])      # about 10 s of single-core oracle work
-        v, sec = cpu_oracle_sample(n_sample)
-        result["cpu_baseline"] = {"value": v, "unit": "particles/s", "cores": 1, "kind": "oracle",
-                                  "sample": f"oracle direct sum at {n_sample} sampled targets of the same "
-                                            f"workload against all {n} sources, {sec:.1f} s single-threaded"}
+        cores = os.cpu_count() or 1
+        n_sample = max(cores, 2 * cores * 32768 // WORKLOAD["n"])   # about 10-30 s of oracle work in all
+        v, sec, used = cpu_oracle_sample(n_sample, cores)
+        result["cpu_baseline"] = {"value": v, "unit": "particles/s", "cores": used, "kind": "oracle",
+                                  "sample": f"oracle direct sum (FP64, Sommerfeld quadrature) at {n_sample} sampled "
+                                            f"targets of the same workload against all {n} sources, spread over "
+                                            f"{used} worker processes on {cores} host cores ({_cpu_model()}), "
+                                            f"{sec:.1f} s"}
     if rank == 0:
         print(json.dumps(result))
     if ws > 1:

@@ -302,6 +302,37 @@ int fmm_layered_direct_noalloc(fmm_layered_t* h, long n_src, const double* src_x
                                double* out, void* stream);
 
 /*
+ * Splitting one problem's components over several GPUs.  The free-space and
+ * reaction components are independent FMMs whose potentials are summed at
+ * the end (eq. totalinteraction; Sec. 4 notes that they can run in
+ * parallel).  Component order: free-space layers 0..L that hold points, then
+ * reaction (l, l', a, b) lexicographically, arrow up = 0 (as reported by
+ * fmm_layered_component_info after an evaluation of all components).
+ *   fmm_layered_set_components: later evaluations of the handle compute only
+ *     components [first, first + count) of that order (count < 0: all from
+ *     `first`; ranges past the end are clipped, an empty range gives zero
+ *     potentials); fmm_layered_eval then returns their sum.  The component
+ *     export reports the evaluated components only.  FMM_ERR_ARG if first < 0.
+ *   fmm_layered_component_work: work estimate of each component of the last
+ *     evaluation (FP64-equivalent flops: M2L translations in the form the
+ *     library runs, near-field pairs -- reaction pairs weighted by their
+ *     contour nodes -- and P2M/L2P per point); writes work[0 .. nc-1] (host)
+ *     and returns nc, or FMM_ERR_ARG if n < nc.  Evaluate all components once
+ *     to split them by this estimate.
+ *   fmm_layered_add_components: out += the potentials of the components of
+ *     the last evaluation, added one component after the other in their
+ *     order -- the same additions, in the same order, as the final sum of
+ *     fmm_layered_eval.  A device buffer holding the sum of the components
+ *     before `first` (computed the same way) therefore becomes bit-identical
+ *     to the all-component result once every later range has been added in
+ *     turn.  Runs on `stream`; FMM_ERR_UNSUPPORTED with FMM_NORM_PAPER (the
+ *     scaling applies to the final sum only).
+ */
+int fmm_layered_set_components(fmm_layered_t* h, int first, int count);
+int fmm_layered_component_work(const fmm_layered_t* h, double* work, int n);
+int fmm_layered_add_components(fmm_layered_t* h, double* out, void* stream);
+
+/*
  * Throughput of dependent FP64 fused multiply-adds on the current device
  * (GFLOP/s, 2 flops per FMA), measured by a short kernel; the denominator of
  * the FP64 roofline.  Returns FMM_OK and writes *gflops.

@@ -58,7 +58,8 @@ EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error
             "fmm_layered_num_components", "fmm_layered_component_info", "fmm_layered_tree_export",
             "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched",
             "fmm_layered_surrogate_train", "fmm_layered_surrogate_report", "fmm_layered_surrogate_set_bound",
-            "fmm_layered_surrogate_grad"]
+            "fmm_layered_surrogate_grad", "fmm_layered_set_components", "fmm_layered_component_work",
+            "fmm_layered_add_components"]
 
 _lib = None
 
@@ -94,6 +95,12 @@ def lib():
     L.fmm_layered_surrogate_report.restype = i
     L.fmm_layered_surrogate_grad.argtypes = [d, d, d, d]
     L.fmm_layered_surrogate_grad.restype = i
+    L.fmm_layered_set_components.argtypes = [v, i, i]
+    L.fmm_layered_set_components.restype = i
+    L.fmm_layered_component_work.argtypes = [v, d, i]
+    L.fmm_layered_component_work.restype = i
+    L.fmm_layered_add_components.argtypes = [v, d, v]
+    L.fmm_layered_add_components.restype = i
     L.fmm_layered_stats.argtypes = [v, ctypes.POINTER(Stats)]
     L.fmm_layered_stats.restype = i
     L.fmm_layered_num_components.argtypes = [v]
@@ -257,6 +264,29 @@ class LayeredFMM:
         ok = np.zeros(n, dtype=np.uint8)
         self._check(lib().fmm_layered_surrogate_report(self.h, _ptr(err), _ptr(ok)))
         return err.reshape(-1, 64), ok.reshape(-1, 64).astype(bool)
+
+    def set_components(self, first=0, count=-1):
+        """Evaluate only components [first, first + count) (count < 0: all)."""
+        self._check(lib().fmm_layered_set_components(self.h, int(first), int(count)))
+
+    def component_work(self):
+        """Work estimate of each component of the last evaluation."""
+        n = lib().fmm_layered_num_components(self.h)
+        w = np.zeros(max(n, 1), dtype=np.float64)
+        rc = lib().fmm_layered_component_work(self.h, _ptr(w), len(w))
+        if rc < 0:
+            self._check(rc)
+        return w[:rc]
+
+    def add_components(self, out, stream=None):
+        """out (complex128 device tensor) += the last evaluation's component
+        potentials, one component after the other in their order."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(out.device)
+        self._check(lib().fmm_layered_add_components(self.h, _ptr(torch.view_as_real(out)),
+                                                     ctypes.c_void_p(stream.cuda_stream)))
+        return out
 
     def stats(self):
         s = Stats()

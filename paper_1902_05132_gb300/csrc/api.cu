@@ -294,6 +294,11 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   build_trees(h, ns, src, q, nt, tgt, gap, st);
   const std::vector<Comp>& comps = h->comps;
   const int nc = (int)comps.size();
+  h->comp_work.assign(nc, 0.0);
+  if (nc == 0) {                       // no component selected: the potentials stay zero
+    h->stats.n_launches = g_fmm_launches - launches0;
+    return;
+  }
   const int nb = h->nboxes;
   const std::vector<int>& lvl = h->lvl_begin;
   int maxlev = 0;
@@ -628,10 +633,12 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   NB.wo = loff + 2 * (nb + 1); NB.wi = ws.wi.as<int>();
   NB.xo = loff + 3 * (nb + 1); NB.xi = ws.xi.as<int>();
   // counters: free pairs, nodes, -, reaction pairs, nodes, surrogate pairs;
-  // then the reaction near-field box: max rho, min z, max z (double bits)
-  unsigned long long* counters = need<unsigned long long>(ws.iota, 9);
-  FMM_CHECK(cudaMemsetAsync(counters, 0, 72, st));
+  // then the reaction near-field box: max rho, min z, max z (double bits);
+  // then the near-field pairs of each component
+  unsigned long long* counters = need<unsigned long long>(ws.iota, 9 + nc);
+  FMM_CHECK(cudaMemsetAsync(counters, 0, 8 * (9 + nc), st));
   FMM_CHECK(cudaMemsetAsync(counters + 7, 0x7F, 8, st));      // min z starts above every finite value
+  NB.comp_pairs = counters + 9;
   launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st,
               (h->flags & FMM_MIXED) != 0);
@@ -648,9 +655,10 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaGetLastError());
   E.mark(8, st);
   int herr = 0;
-  unsigned long long hc[9];
+  std::vector<unsigned long long> hcv(9 + nc);
+  unsigned long long* hc = hcv.data();
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(hc, counters, 72, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(hc, counters, 8 * (9 + nc), cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
   if (herr & 16) throw FmmError(FMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait on an mbarrier expired");
   if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair without an operator");
@@ -679,6 +687,29 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     h->stats.reac_near_z_max = any ? bx[2] : 0.0;
   }
   h->stats.n_launches = g_fmm_launches - launches0;
+  // work estimate per component (FP64-equivalent flops; used to split the
+  // components over GPUs): M2L 8 complex MACs per operator entry and V pair in
+  // the form the library runs, near field 30 per free-space pair and 60 per
+  // contour node of a reaction pair, P2M and L2P 18 (p+1)^2 per point
+  {
+    const double P2 = (double)P;
+    double free_pair = 0, reac_pair = 0;
+    for (int n = 0; n <= p; ++n) free_pair += 2.0 * (2 * n + 1) * (2 * n + 1);
+    for (int m = -p; m <= p; ++m) free_pair += (double)(p + 1 - abs(m)) * (p + 1 - abs(m));
+    if (!rot_shifts) free_pair = P2 * P2;
+    const double npp = (p + 1) * (p + 2) / 2.0, nmm = p * (p + 1) / 2.0;
+    reac_pair = npp * npp + nmm * nmm;
+    std::vector<long> vcount(nc, 0);
+    for (int b = 0; b < nb; ++b) vcount[bcomp[b]] += lo_all[b + 1] - lo_all[b];
+    const double nodes_per_pair = hc[3] ? (double)hc[4] / (double)hc[3] : 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const bool reac = comps[c].kind == CK_REAC;
+      const double pairs = (double)hc[9 + c];
+      h->comp_work[c] = 8.0 * (reac ? reac_pair : free_pair) * vcount[c] +
+                        (reac ? 60.0 * nodes_per_pair * pairs : 30.0 * pairs) +
+                        18.0 * P2 * (double)(comps[c].ns + comps[c].nt);
+    }
+  }
 }
 
 extern "C" int fmm_layered_eval(fmm_layered_t* h, long ns, const double* src, const double* q, long nt,
@@ -795,6 +826,51 @@ extern "C" int fmm_layered_eval_host(fmm_layered_t* h, long ns, const double* sr
   }
   bs.release(); bq.release(); bt.release(); bo.release();
   return rc;
+}
+
+// ---------------------------------------------------------------- components over GPUs
+extern "C" int fmm_layered_set_components(fmm_layered_t* h, int first, int count) {
+  if (!h) return FMM_ERR_ARG;
+  h->err.clear();
+  if (first < 0) {
+    h->err = "first component must be >= 0";
+    return FMM_ERR_ARG;
+  }
+  h->comp_first = first;
+  h->comp_count = count < 0 ? -1 : count;
+  return FMM_OK;
+}
+
+extern "C" int fmm_layered_component_work(const fmm_layered_t* h, double* work, int n) {
+  if (!h || (n > 0 && !work)) return FMM_ERR_ARG;
+  const int nc = (int)h->comp_work.size();
+  if (n < nc) return FMM_ERR_ARG;
+  for (int c = 0; c < nc; ++c) work[c] = h->comp_work[c];
+  return nc;
+}
+
+extern "C" int fmm_layered_add_components(fmm_layered_t* h, double* out, void* stream) {
+  if (!h) return FMM_ERR_ARG;
+  h->err.clear();
+  if (h->flags & FMM_NORM_PAPER) {
+    h->err = "adding component potentials is defined in the physical normalization only (FMM_NORM_PAPER is set)";
+    return FMM_ERR_UNSUPPORTED;
+  }
+  if (h->ntgt_last > 0 && !out) {
+    h->err = "invalid argument";
+    return FMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    const std::vector<Comp>& comps = h->comps;
+    for (size_t c = 0; c < comps.size(); ++c)
+      launch_scatter_add(comps[c].nt, h->ws.tidx.as<int>() + comps[c].to, h->ws.phi.as<cplx>() + comps[c].to, out, st);
+    FMM_CHECK(cudaGetLastError());
+  } catch (FmmError& e) {
+    h->err = e.msg;
+    return e.code;
+  }
+  return FMM_OK;
 }
 
 extern "C" int fmm_layered_measure_fp64_peak(double* gflops) {

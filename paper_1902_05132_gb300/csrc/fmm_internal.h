@@ -223,7 +223,13 @@ struct fmm_layered {
   SurrState surr;
   fmm_stats_t stats{};
   std::string err;
+  // components evaluated: [comp_first, comp_first + comp_count) of the full
+  // ordered list (comp_count < 0: all)
+  int comp_first = 0, comp_count = -1;
   // state of the last evaluation (for export)
+  int n_comp_all = 0;                 // components of the full list
+  int comp_first_eval = 0;            // global index of comps[0]
+  std::vector<double> comp_work;      // work estimate per evaluated component
   std::vector<Comp> comps;
   std::vector<int> lvl_begin;         // global box index where each level starts
   int nboxes = 0;
@@ -277,7 +283,11 @@ struct RuleView {
   SurrView surr;           // learned surrogate of the reaction components (w == nullptr: none)
 };
 struct NearComp { int kind, l, lp, a, b; double k; double dref; long coef_off; };
-struct NearBoxes { const int *comp, *lev, *sb, *se, *tb, *te, *parent; const int *uo, *ui, *wo, *wi, *xo, *xi; };
+struct NearBoxes {
+  const int *comp, *lev, *sb, *se, *tb, *te, *parent;
+  const int *uo, *ui, *wo, *wi, *xo, *xi;
+  unsigned long long* comp_pairs;     // near-field pairs per component (added; may be null)
+};
 struct DirectMedium { int L1; double k[FMM_MAXL], d[FMM_MAXL]; };
 
 

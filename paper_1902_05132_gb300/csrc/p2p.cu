@@ -204,6 +204,7 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
     atomicAdd(&counters[1], my_nodes);
     if (my_surr) atomicAdd(&counters[2], my_surr);
   }
+  if (B.comp_pairs && my_pairs) atomicAdd(&B.comp_pairs[B.comp[T]], my_pairs);
 }
 
 // Reaction components of the near field (U, W and X lists of reaction target
@@ -235,6 +236,25 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leave
   const NearComp nc = ncs[B.comp[T]];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = (int)(nc.coef_off / R.Q);
+  // leaves without near-field entries (the usual case with the interface
+  // rule of the reaction trees) leave at once
+  __shared__ int s_any;
+  if (threadIdx.x == 0) {
+    int any = (B.uo[T + 1] > B.uo[T]) || (B.wo[T + 1] > B.wo[T]);
+    for (int A = T; !any && A >= 0; A = B.parent[A]) any = B.xo[A + 1] > B.xo[A];
+    s_any = any;
+  }
+  __syncthreads();
+  if (!s_any) return;
+  // the component's network, summed to FP32, in shared memory (only when a
+  // surrogate is attached: the launch then gives SURR_NINF floats)
+  extern __shared__ float s_net[];
+  if (R.surr.w) {
+    const __nv_bfloat16* hi = R.surr.w + (long)slot * 2 * SURR_NINF;
+    for (int i = threadIdx.x; i < SURR_NINF; i += blockDim.x)
+      s_net[i] = __bfloat162float(hi[i]) + __bfloat162float(hi[SURR_NINF + i]);
+    __syncthreads();
+  }
   const cplx* coef = R.coef + nc.coef_off;
   const cplx* kzl = R.kz + (long)nc.l * R.Q;
   const cplx* kzp = R.kz + (long)nc.lp * R.Q;
@@ -278,7 +298,7 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leave
             float xin[3];
             int cell;
             if (surr_inputs(R.surr, rho, zt, zs, xin, &cell) && R.surr.ok[slot * SURR_CELLS + cell]) {
-              const float2 v = surr_forward(R.surr.w + (long)slot * 2 * SURR_NINF, xin, cell);
+              const float2 v = surr_forward_f32(s_net, xin, cell);
               const double f = 1.0 / (4.0 * FMM_PI * sqrt(rho * rho + (zt + zs) * (zt + zs)));
               cfma(acc, C((double)v.x * f, (double)v.y * f), qs);
               by_net = true;
@@ -322,6 +342,7 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leave
       atomicAdd(&counters[0], my_pairs);
       atomicAdd(&counters[1], my_nodes);
       if (my_surr) atomicAdd(&counters[2], my_surr);
+      if (B.comp_pairs) atomicAdd(&B.comp_pairs[B.comp[T]], my_pairs);
     }
   }
   if (box) {
@@ -494,7 +515,12 @@ void launch_surr_samples(long n, long nper, const int* slots, int L1, SurrView b
 void launch_near_reac(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
                       const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters,
                       unsigned long long* box, cudaStream_t st) {
-  if (n) LAUNCH(k_near_reac<<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters, box));
+  if (!n) return;
+  const size_t smem = R.surr.w ? sizeof(float) * SURR_NINF : 0;
+  // the network takes more than the default 48 KB (set per call: per device, cheap)
+  FMM_CHECK(cudaFuncSetAttribute(k_near_reac, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * SURR_NINF)));
+  LAUNCH(k_near_reac<<<n, 128, smem, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters, box));
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,

@@ -120,6 +120,62 @@ __device__ inline void surr_features(const __nv_bfloat16* __restrict__ hi, const
   for (int j = 0; j < SURR_H; ++j) f[j] = a[j];
 }
 
+// The same forward pass with the parameters already summed to FP32 (hi + lo,
+// exact) and laid out as in the inference parameters (hidden layers, then
+// the cell output layers), e.g. staged in shared memory.  Same operations in
+// the same order as surr_features + the output layer below: bit-identical
+// results.  Fully unrolled so that the layer activations stay in registers.
+__device__ __forceinline__ float2 surr_forward_f32(const float* __restrict__ w, const float* x, int cell) {
+  float a[SURR_H], f[SURR_H];
+  const float xi0 = surr_hilo(x[0]), xi1 = surr_hilo(x[1]), xi2 = surr_hilo(x[2]);
+#pragma unroll
+  for (int j = 0; j < SURR_H; ++j) {
+    float s = w[SURR_B1 + j];
+    s = fmaf(w[SURR_W1 + j * 3 + 0], xi0, s);
+    s = fmaf(w[SURR_W1 + j * 3 + 1], xi1, s);
+    s = fmaf(w[SURR_W1 + j * 3 + 2], xi2, s);
+    a[j] = surr_hilo(surr_gelu(s));
+  }
+#pragma unroll
+  for (int j = 0; j < SURR_H; ++j) {
+    float s = w[SURR_B2 + j];
+    const float4* r = reinterpret_cast<const float4*>(w + SURR_W2 + j * SURR_H);
+#pragma unroll
+    for (int i = 0; i < SURR_H / 4; ++i) {
+      const float4 v = r[i];
+      s = fmaf(v.x, a[4 * i], s);
+      s = fmaf(v.y, a[4 * i + 1], s);
+      s = fmaf(v.z, a[4 * i + 2], s);
+      s = fmaf(v.w, a[4 * i + 3], s);
+    }
+    f[j] = surr_hilo(surr_gelu(s));
+  }
+#pragma unroll
+  for (int j = 0; j < SURR_H; ++j) {
+    float s = w[SURR_B3 + j];
+    const float4* r = reinterpret_cast<const float4*>(w + SURR_W3 + j * SURR_H);
+#pragma unroll
+    for (int i = 0; i < SURR_H / 4; ++i) {
+      const float4 v = r[i];
+      s = fmaf(v.x, f[4 * i], s);
+      s = fmaf(v.y, f[4 * i + 1], s);
+      s = fmaf(v.z, f[4 * i + 2], s);
+      s = fmaf(v.w, f[4 * i + 3], s);
+    }
+    a[j] = surr_hilo(surr_gelu(s));
+  }
+  float o[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float* r = w + SURR_NTRUNK + (cell * 2 + k) * SURR_HEAD_N;
+    float s = r[SURR_H];
+#pragma unroll
+    for (int i = 0; i < SURR_H; ++i) s = fmaf(r[i], a[i], s);
+    o[k] = s;
+  }
+  return make_float2(o[0], o[1]);
+}
+
 // Forward pass of one component's network for one input in `cell`.
 __device__ inline float2 surr_forward(const __nv_bfloat16* __restrict__ W, const float* x, int cell) {
   const __nv_bfloat16* hi = W;

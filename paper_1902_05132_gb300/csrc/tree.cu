@@ -567,7 +567,24 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
         }
       }
     }
+  // the selected range of components (fmm_layered_set_components)
+  h->n_comp_all = (int)comps.size();
+  {
+    const int first = std::min(std::max(h->comp_first, 0), h->n_comp_all);
+    const int last = h->comp_count < 0 ? h->n_comp_all : std::min(h->n_comp_all, first + h->comp_count);
+    comps = std::vector<Comp>(comps.begin() + first, comps.begin() + std::max(first, last));
+    h->comp_first_eval = first;
+  }
   const int nc = (int)comps.size();
+  if (nc == 0) {
+    h->nboxes = 0;
+    h->lvl_begin.assign(23, 0);
+    h->stats.n_components = 0;
+    h->stats.n_boxes = 0;
+    h->stats.max_level = 0;
+    h->stats.n_v_pairs = 0;
+    return;
+  }
   long so = 0, to = 0;
   std::vector<CompDev> cdev(nc);
   for (int ci = 0; ci < nc; ++ci) {
