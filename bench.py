@@ -24,7 +24,12 @@ Extra keys of the JSON line:
 
 Multi-GPU (torchrun): every rank evaluates its own independent problem of the
 same size (weak scaling, no data-path collective); the barrier and the
-max-over-ranks time use torch.distributed.  --impl reference times the CPU
+max-over-ranks time use torch.distributed.  With --split components the
+ranks share ONE problem instead: each evaluates a contiguous range of its
+components (chosen from the work estimate of one all-component evaluation)
+and the potentials are summed along the ranks in component order
+(paper_1902_05132_gb300.distributed.chain_sum over NCCL), inside the timed
+step (strong scaling).  --impl reference times the CPU
 oracle (the only reference implementation this project has) on a bounded
 sample of the same workload, on all host cores.
 """
@@ -384,6 +389,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--workload", default="three-layer-32768", choices=sorted(WORKLOADS))
+    ap.add_argument("--split", default="problems", choices=["problems", "components"])
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
@@ -402,7 +408,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     _build.build()
-    w = workloads.three_layer(n=WORKLOAD["n"], seed=rank, p=WORKLOAD["p"], leaf=WORKLOAD["leaf"],
+    split = args.split == "components" and ws > 1
+    w = workloads.three_layer(n=WORKLOAD["n"], seed=0 if split else rank, p=WORKLOAD["p"], leaf=WORKLOAD["leaf"],
                               complex_charges=WORKLOAD["complex"])
     solver = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
     src = torch.tensor(w["src"], device=dev)
@@ -411,8 +418,25 @@ def main():
     out = torch.empty(len(w["tgt"]), dtype=torch.complex128, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    step = None
+    if split:
+        from paper_1902_05132_gb300 import distributed
+        solver.eval(src, q, tgt, out=out)                    # plan: work of every component
+        work = torch.tensor(solver.component_work(), dtype=torch.float64, device=dev)
+        dist.broadcast(work, src=0)
+        first, count = distributed.partition(work.cpu().tolist(), ws)[rank]
+        solver.set_components(first, count)
+        part = torch.empty_like(out)
+
+        def step():
+            solver.eval(src, q, tgt, out=part)
+            distributed.chain_sum(out, solver.add_components, rank, ws, dist,
+                                  own_result=part if rank == 0 else None)
+    else:
+        def step():
+            solver.eval(src, q, tgt, out=out)
     for _ in range(max(3, args.warmup)):
-        solver.eval(src, q, tgt, out=out)
+        step()
     torch.cuda.synchronize()
     clock_dir = os.environ.get("FMM_BENCH_CLOCKS_DIR") or tempfile.mkdtemp(prefix="fmm_bench_")
     os.makedirs(clock_dir, exist_ok=True)
@@ -430,7 +454,7 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        solver.eval(src, q, tgt, out=out)
+        step()
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -446,6 +470,19 @@ def main():
         sampler.wait()
     n = len(w["tgt"])
     ms_per_step, value = aggregate(sum(ms), args.steps, n, ws, dev)
+    if split:                     # one problem shared by all ranks: N particles per step
+        value /= ws
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD["name"], "parallelism": f"components of one problem over {ws} GPUs, "
+                           "chain sum of the potentials in component order (NCCL)",
+                           "l2": "flushed between steps (256 MB write)"},
+                "clocks": _clock_summary(clock_path), "gpu_launches": launches}))
+        dist.destroy_process_group()
+        return
 
     # first evaluation of a fresh solver: translation operators not cached yet
     cold = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])

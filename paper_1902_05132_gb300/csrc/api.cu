@@ -41,8 +41,8 @@ void launch_near_reac(const int* leaves, int n, NearBoxes B, const NearComp* ncs
                       const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters,
                       unsigned long long* box, cudaStream_t st);
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
-                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st,
-                 bool f32);
+                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, int* err,
+                 cudaStream_t st, bool f32);
 double measure_fp64_peak_impl();
 void launch_direct(long nt, const double* tgt, long ns, const double* src, const double* q, DirectMedium md,
                    RuleView R, const cplx* coef_all, double* out, cudaStream_t st);
@@ -640,7 +640,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaMemsetAsync(counters + 7, 0x7F, 8, st));      // min z starts above every finite value
   NB.comp_pairs = counters + 9;
   launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
-              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, st,
+              ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, err, st,
               (h->flags & FMM_MIXED) != 0);
   E.mark(6, st);
   RuleView rv_reac = make_rule_view(h->rule, coef);
@@ -661,6 +661,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaMemcpyAsync(hc, counters, 8 * (9 + nc), cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
   if (herr & 16) throw FmmError(FMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait on an mbarrier expired");
+  if (herr & 32) throw FmmError(FMM_ERR_TIMEOUT, "near field: a bounded wait for the source copies expired");
   if (herr) throw FmmError(FMM_ERR_UNSUPPORTED, "reaction M2L pair without an operator");
   h->stats.ms_eval = ms_since(t2);
   h->stats.gpu_ms_tree = E.ms(0, 1);

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "fmm_internal.h"
 
 
@@ -205,6 +206,169 @@ __global__ void k_near(const int* __restrict__ leaves, NearBoxes B, const NearCo
     if (my_surr) atomicAdd(&counters[2], my_surr);
   }
   if (B.comp_pairs && my_pairs) atomicAdd(&B.comp_pairs[B.comp[T]], my_pairs);
+}
+
+// Free-space near field in FP64 (U, W and X lists of free-space target
+// leaves; eq. totalinteraction, j != i): one CTA of 256 threads per target
+// leaf.  The sources of U(T), W(T) and X(A) for A = T and its ancestors are
+// gathered in chunks of up to NF_CH points: one thread issues one
+// cp.async.bulk per source-box piece for its positions (the 16-byte aligned
+// cover of the piece's bytes) and one for its charges, all completing on one
+// mbarrier (bounded wait); the CTA then unpacks the positions into
+// structure-of-arrays form (the charges land contiguous already).  Warp w
+// takes targets t = tb + w, tb + w + 8, ...; its lanes split the chunk's
+// sources (lane i: sources i, i + 32, ...) and the partial sums of a target
+// are added by a warp-shuffle reduction, then into the target's sum in
+// shared memory, chunk after chunk in a fixed order.  Targets are taken 256
+// per pass.  On an expired wait the kernel sets bit 32 of *err, waits once
+// more (bounded) for its copies and returns.
+constexpr int NF_THREADS = 256;
+constexpr int NF_CH = 1024;                 // source points per chunk
+constexpr int NF_SEG = 64;                  // source-box pieces per chunk
+constexpr int NF_TG = 256;                  // targets per pass
+constexpr int NF_RAWP = 24 * NF_CH + 16 * NF_SEG;
+// shared memory: raw positions, charges, x/y/z, target sums, 4 piece
+// tables, a 16-byte header (pieces, points) and the mbarrier
+constexpr size_t NF_SMEM = (size_t)NF_RAWP + 16 * NF_CH + 24 * NF_CH + 16 * NF_TG + 4 * 4 * NF_SEG + 16 + 8;
+
+__device__ inline void warp_sum(cplx& v);
+
+__global__ void __launch_bounds__(NF_THREADS) k_near_free(const int* __restrict__ leaves, NearBoxes B,
+                                                         const NearComp* __restrict__ ncs,
+                                                         const double* __restrict__ spos,
+                                                         const cplx* __restrict__ sq,
+                                                         const double* __restrict__ tpos, cplx* __restrict__ phi,
+                                                         unsigned long long* __restrict__ counters,
+                                                         int* __restrict__ err) {
+  const int T = leaves[blockIdx.x];
+  const double k = ncs[B.comp[T]].k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ __align__(128) unsigned char nf_sm[];
+  unsigned char* raw_pos = nf_sm;                                   // [NF_RAWP] bytes
+  cplx* sqv = (cplx*)(raw_pos + NF_RAWP);                           // [NF_CH] charges (copied in place)
+  double* sx = (double*)(sqv + NF_CH);                              // [NF_CH] x, y, z
+  double* sy = sx + NF_CH;
+  double* sz = sy + NF_CH;
+  cplx* acc = (cplx*)(sz + NF_CH);                                  // [NF_TG] target sums
+  int* seg_src = (int*)(acc + NF_TG);                               // first source of each piece
+  int* seg_n = seg_src + NF_SEG;                                    // its points
+  int* seg_at = seg_n + NF_SEG;                                     // its first slot in the chunk
+  int* seg_raw = seg_at + NF_SEG;                                   // byte offset of its first point in raw_pos
+  int* hdr = seg_raw + NF_SEG;                                      // [0]: pieces, [1]: points
+  unsigned long long* bar = (unsigned long long*)(hdr + 4);
+  const uint32_t bar_a = smem_u32(bar);
+  if (threadIdx.x == 0) {
+    mbar_init(bar_a, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const double inv4pi = 1.0 / (4.0 * FMM_PI);
+  unsigned long long my_pairs = 0;
+  uint32_t parity = 0;
+  for (int tg0 = B.tb[T]; tg0 < B.te[T]; tg0 += NF_TG) {
+    const int ntg = min(NF_TG, B.te[T] - tg0);
+    for (int i = threadIdx.x; i < ntg; i += NF_THREADS) acc[i] = C(0, 0);
+    // list walk (thread 0): U(T), W(T), then X(A) for A = T and its ancestors
+    int phase = 0, A = T, e = B.uo[T], e_end = B.uo[T + 1], s_cur = 0, s_end = 0;
+    while (true) {
+      if (threadIdx.x == 0) {
+        int nseg = 0, npts = 0;
+        uint32_t rawp = 0, bytes = 0;
+        // the pieces of this chunk first, then the copies (the barrier must
+        // expect every byte before the first copy can complete)
+        while (npts < NF_CH && nseg < NF_SEG) {
+          if (s_cur >= s_end) {               // next source box of the lists
+            while (e >= e_end && !(phase == 2 && A < 0)) {
+              if (phase == 0) { phase = 1; e = B.wo[T]; e_end = B.wo[T + 1]; }
+              else if (phase == 1) { phase = 2; A = T; e = B.xo[A]; e_end = B.xo[A + 1]; }
+              else {
+                A = B.parent[A];
+                if (A >= 0) { e = B.xo[A]; e_end = B.xo[A + 1]; }
+              }
+            }
+            if (phase == 2 && A < 0) break;
+            const int S = (phase == 0) ? B.ui[e] : (phase == 1) ? B.wi[e] : B.xi[e];
+            ++e;
+            s_cur = B.sb[S];
+            s_end = B.se[S];
+            continue;
+          }
+          const int n = min(s_end - s_cur, NF_CH - npts);
+          const unsigned long long b0 = 24ull * (unsigned long long)s_cur;
+          const unsigned long long a0 = b0 & ~15ull, a1 = (b0 + 24ull * n + 15ull) & ~15ull;
+          const uint32_t lb = (uint32_t)(a1 - a0);
+          seg_src[nseg] = s_cur;
+          seg_n[nseg] = n;
+          seg_at[nseg] = npts;
+          seg_raw[nseg] = (int)(rawp + (uint32_t)(b0 - a0));
+          rawp += lb;
+          bytes += lb + 16u * n;
+          s_cur += n;
+          npts += n;
+          ++nseg;
+        }
+        if (nseg) {
+          mbar_expect_tx(bar_a, bytes);       // the one arrival of this phase
+          for (int g = 0; g < nseg; ++g) {
+            const int s0 = seg_src[g], n = seg_n[g];
+            const unsigned long long b0 = 24ull * (unsigned long long)s0;
+            const unsigned long long a0 = b0 & ~15ull, a1 = (b0 + 24ull * n + 15ull) & ~15ull;
+            bulk_g2s(smem_u32(raw_pos + (seg_raw[g] - (int)(b0 - a0))), (const unsigned char*)spos + a0,
+                     (uint32_t)(a1 - a0), bar_a);
+            bulk_g2s(smem_u32(sqv + seg_at[g]), sq + s0, 16u * n, bar_a);
+          }
+        }
+        hdr[0] = nseg;
+        hdr[1] = npts;
+      }
+      __syncthreads();
+      const int nseg = hdr[0], npts = hdr[1];
+      if (nseg == 0) break;
+      const bool ok = mbar_wait(bar_a, parity);
+      parity ^= 1u;
+      if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) atomicOr(err, 32);
+        mbar_wait(bar_a, parity ^ 1u);        // the copies of this phase, once more (bounded)
+        return;
+      }
+      // unpack the positions
+      for (int j = threadIdx.x; j < npts; j += NF_THREADS) {
+        int g = 0;
+        while (g + 1 < nseg && seg_at[g + 1] <= j) ++g;
+        const double* p = (const double*)(raw_pos + seg_raw[g]) + 3 * (j - seg_at[g]);
+        sx[j] = p[0];
+        sy[j] = p[1];
+        sz[j] = p[2];
+      }
+      __syncthreads();
+      for (int ti = warp; ti < ntg; ti += NF_THREADS / 32) {
+        const int t = tg0 + ti;
+        const double x = tpos[3 * t], y = tpos[3 * t + 1], z = tpos[3 * t + 2];
+        cplx part = C(0, 0);
+        for (int j = lane; j < npts; j += 32) {
+          const double dx = x - sx[j], dy = y - sy[j], dz = z - sz[j];
+          if (dx == 0.0 && dy == 0.0 && dz == 0.0) continue;   // bitwise-identical points (j = i)
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          const double rinv = rsqrt(r2);
+          double sn, cs;
+          sincos(k * (r2 * rinv), &sn, &cs);
+          const double f = rinv * inv4pi;
+          cfma(part, C(cs * f, sn * f), sqv[j]);
+          ++my_pairs;
+        }
+        warp_sum(part);
+        if (lane == 0) acc[ti] = cadd(acc[ti], part);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ntg; i += NF_THREADS) phi[tg0 + i] = cadd(phi[tg0 + i], acc[i]);
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, o);
+  if (lane == 0 && my_pairs) {
+    if (counters) atomicAdd(&counters[0], my_pairs);
+    if (B.comp_pairs) atomicAdd(&B.comp_pairs[B.comp[T]], my_pairs);
+  }
 }
 
 // Reaction components of the near field (U, W and X lists of reaction target
@@ -524,11 +688,15 @@ void launch_near_reac(const int* leaves, int n, NearBoxes B, const NearComp* ncs
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
-                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, cudaStream_t st,
-                 bool f32) {
+                 const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters, int* err,
+                 cudaStream_t st, bool f32) {
   if (!n) return;
-  if (f32) LAUNCH(k_near<true><<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
-  else LAUNCH(k_near<false><<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
+  if (f32) {
+    LAUNCH(k_near<true><<<n, 128, 0, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters));
+  } else {
+    FMM_CHECK(cudaFuncSetAttribute(k_near_free, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NF_SMEM));
+    LAUNCH(k_near_free<<<n, NF_THREADS, NF_SMEM, st>>>(leaves, B, ncs, spos, sq, tpos, phi, counters, err));
+  }
 }
 
 // Dependent FP64 FMA chains (8 independent chains per thread).

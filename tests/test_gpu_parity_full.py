@@ -72,3 +72,57 @@ def test_accuracy_improves_with_p():
         s.close()
         print("p=%d: %.2e" % (p, e))
         assert e < 1e-7, (p, e)
+
+
+FULL = os.path.join(os.path.dirname(__file__), "golden", "oracle_values_full.npz")
+
+
+def _full():
+    if not os.path.exists(FULL):
+        pytest.skip("tests/golden/oracle_values_full.npz not written (tests/golden/make_golden_full.py)")
+    return np.load(FULL)
+
+
+def test_three_layer_full_size_2000_targets_element_by_element():
+    # three-layer N = 32,768, p = 8, leaf 64 (the bench workload and launch
+    # configuration): every one of 2,000 sampled potentials against the oracle
+    # direct sum (the method's truncation at p = 8 bounds the difference), and
+    # 200 of them against the oracle FMM (same method: FP64 rounding only)
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    g = _full()
+    w = workloads.three_layer()
+    s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
+    src, q, tgt = to_dev(torch, w)
+    got = s.eval(src, q, tgt).cpu().numpy()
+    sel, ref = g["three_layer_sel2000"], g["three_layer_direct2000"]
+    e2 = rel_l2(got[sel], ref)
+    emax = float(np.max(np.abs(got[sel] - ref)) / np.max(np.abs(ref)))
+    fsel, fref = g["three_layer_fmm_sel"], g["three_layer_fmm200"]
+    f2 = rel_l2(got[fsel], fref)
+    fmax = float(np.max(np.abs(got[fsel] - fref)) / np.max(np.abs(fref)))
+    print(f"N=32768 p=8: vs oracle direct sum (2000 targets) rel L2 {e2:.2e}, max {emax:.2e}; "
+          f"vs oracle FMM (200 targets) rel L2 {f2:.2e}, max {fmax:.2e}")
+    assert e2 < 1e-6 and emax < 1e-6, (e2, emax)
+    assert f2 < 1e-9 and fmax < 1e-9, (f2, fmax)
+
+
+def test_three_layer_2e20_complex_charges_vs_oracle():
+    # N = 2^20, p = 10, complex charges (the large configuration): the FP64
+    # path within 1e-6 and the mixed form within 1e-5 of the oracle direct sum
+    # at 128 sampled targets
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    g = _full()
+    w = workloads.three_layer(n=1048576, p=10, complex_charges=True)
+    src, q, tgt = to_dev(torch, w)
+    sel, ref = g["three_layer_1m_sel"], g["three_layer_1m_direct"]
+    errs = {}
+    for form, kw in (("fp64", {}), ("mixed", {"mixed": True})):
+        s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], **kw)
+        got = s.eval(src, q, tgt).cpu().numpy()
+        s.close()
+        errs[form] = (rel_l2(got[sel], ref), float(np.max(np.abs(got[sel] - ref)) / np.max(np.abs(ref))))
+    print("N=2^20 p=10 complex charges vs oracle direct sum (128 targets):", errs)
+    assert errs["fp64"][0] < 1e-6 and errs["fp64"][1] < 1e-6, errs
+    assert errs["mixed"][0] < 1e-5 and errs["mixed"][1] < 1e-5, errs
