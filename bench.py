@@ -18,6 +18,9 @@ Extra keys of the JSON line:
              near field, then the mixed + surrogate form (FMM_MIXED |
              FMM_SURROGATE) with the network trained on the near-field box
   large      N = 2^20, p = 10, complex charges: FP64 and mixed forms
+  paper_table  the paper's timing study (Sec. 4, Table 1): irregular domains,
+             p = 4, N = 618,256 .. 2,861,288; all components, the 3
+             free-space ones and the 3 reaction ones the table selects
   errors     each form against oracle values stored in
              tests/golden/oracle_values_full.npz (written offline by
              tests/golden/make_golden_full.py from the oracle alone)
@@ -379,6 +382,48 @@ def large_leg(pkg, torch, dev, args, flush, stream, gold):
     return res
 
 
+# the paper's Table 1 (Sec. 4): N, free-space time (all 3 components) and
+# reaction time (3 selected components) on 36 Xeon E5-2699 v4 cores, p = 4
+PAPER_TABLE_36 = {618256: (2.29, 2.74), 1128556: (5.00, 3.21), 1862568: (11.45, 3.59), 2861288: (12.60, 3.90)}
+
+
+def paper_table_leg(pkg, torch, dev, flush, stream):
+    """The paper's timing study (Sec. 4, Table 1) on its own workload: the
+    irregular domains of workloads.paper_domains scaled to the table's N,
+    p = 4, FP64.  Times all 19 components, the 3 free-space components, and
+    the 3 reaction components the table selects (u_00^{up up}, u_11^{up up},
+    u_22^{down down}: components 3, 9 and 18 of the library's order)."""
+    from paper_1902_05132_gb300 import workloads
+    rows = []
+    for n, (t_free36, t_reac36) in PAPER_TABLE_36.items():
+        base = np.array([912, 640, 1296], dtype=float)
+        counts = np.floor(n * base / base.sum()).astype(int)
+        counts[0] += n - counts.sum()
+        w = workloads.paper_domains(counts=tuple(int(c) for c in counts), p=4, leaf=64)
+        src = torch.tensor(w["src"], device=dev)
+        q = torch.tensor(w["q"], device=dev)
+        tgt = torch.tensor(w["tgt"], device=dev)
+        out = torch.empty(n, dtype=torch.complex128, device=dev)
+        row = {"n": n}
+        for name, ranges in (("all", [(0, -1)]), ("free3", [(0, 3)]), ("reac3", [(3, 1), (9, 1), (18, 1)])):
+            tot = 0.0
+            for first, count in ranges:
+                s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=4, leaf=64)
+                s.set_components(first, count)
+                ms, _ = timed_evals(torch, s, src, q, tgt, out, 2, 1, flush, stream)
+                s.close()
+                tot += statistics.mean(ms)
+            row[name + "_ms"] = tot
+        row["particles_per_s"] = n / (row["all_ms"] * 1e-3)
+        row["free3_particles_per_s"] = n / (row["free3_ms"] * 1e-3)
+        row["paper_36_cores_s"] = {"free3": t_free36, "reac3": t_reac36,
+                                   "free3_particles_per_s": n / t_free36}
+        rows.append(row)
+        del src, q, tgt, out
+    return {"workload": "paper domains (Sec. 4), k=(1.2,1.5,1.8), p=4, leaf 64, FP64; the paper's times are "
+                        "2x Xeon E5-2699 v4, 36 cores (context only)", "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,6 +433,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-paper-table", action="store_true")
     ap.add_argument("--workload", default="three-layer-32768", choices=sorted(WORKLOADS))
     ap.add_argument("--split", default="problems", choices=["problems", "components"])
     args = ap.parse_args()
@@ -561,6 +607,8 @@ def main():
         result["surrogate"] = surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, gold)
     if not args.no_large and ws == 1:
         result["large"] = large_leg(pkg, torch, dev, args, flush, stream, _golden())
+    if not args.no_paper_table and ws == 1:
+        result["paper_table"] = paper_table_leg(pkg, torch, dev, flush, stream)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         cores = os.cpu_count() or 1
         n_sample = max(cores, 2 * cores * 32768 // WORKLOAD["n"])   # about 10-30 s of oracle work in all

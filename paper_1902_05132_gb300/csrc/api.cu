@@ -169,11 +169,11 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   DevBuf* wsb[] = {&ws.slayer, &ws.tlayer, &ws.sorder, &ws.torder, &ws.iota, &ws.ltmp, &ws.counts, &ws.bbox,
                    &ws.gap, &ws.flags, &ws.spos_u, &ws.sq_u, &ws.skey_u, &ws.sval_u, &ws.sidx_u, &ws.tpos_u,
                    &ws.tkey_u, &ws.tval_u, &ws.tidx_u, &ws.skey, &ws.sperm, &ws.spos, &ws.sq, &ws.sidx,
-                   &ws.slocal, &ws.tkey, &ws.tperm, &ws.tpos, &ws.tidx, &ws.tlocal, &ws.segs, &ws.segl,
+                   &ws.slocal, &ws.tkey, &ws.tperm, &ws.tpos, &ws.tidx, &ws.tlocal, &ws.segs, &ws.segl, &ws.segs_keys,
                    &ws.bcomp, &ws.blevel, &ws.bprefix, &ws.bsb, &ws.bse, &ws.btb, &ws.bte, &ws.bparent,
                    &ws.bchild0, &ws.bnchild, &ws.bcoord, &ws.lvlcnt, &ws.lvlscan, &ws.lvl_begin, &ws.lcnt,
                    &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
-                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.cub_tmp};
+                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.sort_tmp};
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
                   &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,

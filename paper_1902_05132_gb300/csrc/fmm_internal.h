@@ -133,7 +133,7 @@ struct Workspace {
   DevBuf spos_u, sq_u, skey_u, sval_u, sidx_u, tpos_u, tkey_u, tval_u, tidx_u;
   // ... and sorted by (component, key)
   DevBuf skey, sperm, spos, sq, sidx, slocal, tkey, tperm, tpos, tidx, tlocal;
-  DevBuf segs, segl;
+  DevBuf segs, segl, segs_keys;
   // boxes
   DevBuf bcomp, blevel, bprefix, bsb, bse, btb, bte, bparent, bchild0, bnchild, bcoord;
   DevBuf lvlcnt, lvlscan, lvl_begin;
@@ -151,7 +151,7 @@ struct Workspace {
   // rotation-form free-space M2L: run info, operator jobs, batches, run starts
   DevBuf rot_info, rot_jobs, rot_bat, rot_rs, rot_tab;
   DevBuf out_tmp;
-  DevBuf cub_tmp;
+  DevBuf sort_tmp;
 };
 
 // Translation operators kept across evaluations: they depend only on the box

@@ -7,7 +7,7 @@
 // symmetric basis for reaction pairs), one tiled FP64 complex GEMM per
 // operator produces the translated columns, and a per-target reduction adds
 // them back in V-list order (deterministic), undoing the rotation.
-#include <cub/cub.cuh>
+#include "sort.h"
 
 #include <algorithm>
 #include <vector>
@@ -340,20 +340,15 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
     int* inv = ws.g_inv.as<int>();
     LAUNCH(k_v_owner<<<(nb + 127) / 128, 128, 0, st>>>(nb, voff, owner));
     LAUNCH(k_v_keys<<<(nv + 255) / 256, 256, 0, st>>>(nv, owner, vidx, B, OI, P, keys, vals, err));
-    size_t tb = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, tb, keys, keys2, vals, perm, (int)nv, 0, 64, st);
-    ws.cub_tmp.ensure(tb);
-    cub::DeviceRadixSort::SortPairs(ws.cub_tmp.ptr, tb, keys, keys2, vals, perm, (int)nv, 0, 64, st);
+    // stable sort by operator key (keys and vals are overwritten)
+    dev_sort_pairs(keys, vals, keys2, perm, nv, 0, 64, ws.sort_tmp, st);
     LAUNCH(k_inverse_perm<<<(nv + 255) / 256, 256, 0, st>>>(nv, perm, inv));
     // run-length encode the sorted keys
     ws.g_runs.ensure((8 + 4) * (size_t)nv + 64);
     unsigned long long* ukeys = ws.g_runs.as<unsigned long long>();
     int* counts = (int*)(ukeys + nv);
     int* nruns_d = (int*)(counts + nv);
-    size_t tb2 = 0;
-    cub::DeviceRunLengthEncode::Encode(nullptr, tb2, keys2, ukeys, counts, nruns_d, (int)nv, st);
-    ws.cub_tmp.ensure(tb2);
-    cub::DeviceRunLengthEncode::Encode(ws.cub_tmp.ptr, tb2, keys2, ukeys, counts, nruns_d, (int)nv, st);
+    dev_run_length(keys2, nv, ukeys, counts, nruns_d, ws.sort_tmp, st);
     int nruns = 0;
     FMM_CHECK(cudaMemcpyAsync(&nruns, nruns_d, 4, cudaMemcpyDeviceToHost, st));
     FMM_CHECK(cudaStreamSynchronize(st));

@@ -36,13 +36,13 @@
 //    descendants of T's colleagues whose parent is adjacent to T but which are
 //    not; X(T) source leaves coarser than T adjacent to parent(T) but not to T.
 //    Every list is sorted by box number.
-#include <cub/cub.cuh>
 
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "fmm_internal.h"
+#include "sort.h"
 
 #define FLAG_ON_INTERFACE 1
 #define FLAG_NONFINITE 2
@@ -440,10 +440,37 @@ static T* need(DevBuf& b, size_t n) {
 }
 
 static void exclusive_scan(Workspace& ws, const int* in, int* out, int n, cudaStream_t st) {
-  size_t tb = 0;
-  cub::DeviceScan::ExclusiveSum(nullptr, tb, in, out, n, st);
-  ws.cub_tmp.ensure(tb);
-  cub::DeviceScan::ExclusiveSum(ws.cub_tmp.ptr, tb, in, out, n, st);
+  dev_exclusive_scan(in, out, n, ws.sort_tmp, st);
+}
+
+// keys for the stable partition of points by layer: (layer, position)
+__global__ void k_layer_keys(long n, const unsigned char* __restrict__ layer, unsigned long long* __restrict__ key,
+                             int* __restrict__ val) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  key[i] = layer[i];
+  val[i] = (int)i;
+}
+
+// component of each sorted point (by its position in the concatenated,
+// component-ordered list) as the key of the last, stable pass
+__global__ void k_comp_keys(long n, const int* __restrict__ pos, const long* __restrict__ seg_begin, int nseg,
+                            unsigned long long* __restrict__ key) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = pos[i];
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (seg_begin[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  key[i] = (unsigned long long)lo;
+}
+
+__global__ void k_gather_keys(long n, const int* __restrict__ pos, const unsigned long long* __restrict__ in,
+                              unsigned long long* __restrict__ out) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[pos[i]];
 }
 
 struct ClassifyOut {
@@ -502,18 +529,15 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
   int* sorder = need<int>(ws.sorder, ns);
   int* torder = need<int>(ws.torder, nt);
   {
-    // iota values, radix sort on the layer byte (stable)
-    int* iota = need<int>(ws.iota, std::max(ns, nt));
-    unsigned char* ktmp = need<unsigned char>(ws.ltmp, std::max(ns, nt));
+    // stable radix sort on the layer byte, values = positions
     const long ni = std::max(ns, nt);
-    LAUNCH(k_iota<<<(unsigned)((ni + 255) / 256), 256, 0, st>>>(ni, iota));
+    unsigned long long* kbuf = need<unsigned long long>(ws.ltmp, 2 * (size_t)ni);
+    int* vbuf = need<int>(ws.iota, ni);
     for (int set = 0; set < 2; ++set) {
       long n = set ? nt : ns;
       if (!n) continue;
-      size_t tb = 0;
-      cub::DeviceRadixSort::SortPairs(nullptr, tb, set ? tl : sl, ktmp, iota, set ? torder : sorder, (int)n, 0, 8, st);
-      ws.cub_tmp.ensure(tb);
-      cub::DeviceRadixSort::SortPairs(ws.cub_tmp.ptr, tb, set ? tl : sl, ktmp, iota, set ? torder : sorder, (int)n, 0, 8, st);
+      LAUNCH(k_layer_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, set ? tl : sl, kbuf, vbuf));
+      dev_sort_pairs(kbuf, vbuf, kbuf + ni, set ? torder : sorder, n, 0, 8, ws.sort_tmp, st);
     }
   }
   ClassifyOut co;
@@ -677,15 +701,25 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
   int* sperm = need<int>(ws.sperm, NS);
   int* tperm = need<int>(ws.tperm, NT);
   for (int set = 0; set < 2; ++set) {
+    // stable sort by the 63-bit key, then (stable) by component: the order
+    // (component, key, position in the component's list)
     long n = set ? NT : NS;
     if (!n) continue;
-    size_t tb = 0;
-    const int* seg = dsegs + (set ? nc + 1 : 0);
-    cub::DeviceSegmentedRadixSort::SortPairs(nullptr, tb, set ? tkey_u : skey_u, set ? tkey : skey,
-                                             set ? tval_u : sval_u, set ? tperm : sperm, (int)n, nc, seg, seg + 1, 0, 63, st);
-    ws.cub_tmp.ensure(tb);
-    cub::DeviceSegmentedRadixSort::SortPairs(ws.cub_tmp.ptr, tb, set ? tkey_u : skey_u, set ? tkey : skey,
-                                             set ? tval_u : sval_u, set ? tperm : sperm, (int)n, nc, seg, seg + 1, 0, 63, st);
+    unsigned long long* ku = set ? tkey_u : skey_u;
+    unsigned long long* kd = set ? tkey : skey;
+    int* vu = set ? tval_u : sval_u;
+    int* vd = set ? tperm : sperm;
+    // keep the unsorted keys: the passes overwrite their input
+    unsigned long long* kcopy = need<unsigned long long>(ws.segs_keys, 2 * (size_t)n);
+    FMM_CHECK(cudaMemcpyAsync(kcopy, ku, 8 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    dev_sort_pairs(kcopy, vu, kd, vd, n, 0, 63, ws.sort_tmp, st);
+    if (nc > 1) {
+      unsigned long long* ck = kcopy + n;
+      LAUNCH(k_comp_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, vd, dsegl + (set ? nc + 1 : 0), nc, ck));
+      FMM_CHECK(cudaMemcpyAsync(vu, vd, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+      dev_sort_pairs(ck, vu, kcopy, vd, n, 0, nc > 256 ? 16 : 8, ws.sort_tmp, st);
+      LAUNCH(k_gather_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, vd, ku, kd));
+    }
   }
   double* spos = need<double>(ws.spos, 3 * NS);
   cplx* sqs = need<cplx>(ws.sq, NS);
