@@ -221,6 +221,31 @@ __device__ inline bool refine_box(int level, int leaf, int ns, int nt, bool spli
   return false;
 }
 
+// Children of box b (one warp per box): lane o = 0..8 finds the first source
+// key at or above the start of child octant o's key range (o = 8: the end of
+// the box's range), lane 16 + o the same among the target keys, so child o
+// holds sources [s(o), s(o+1)) and targets [t(o), t(o+1)).  The searches run
+// side by side instead of one after the other.
+__device__ inline unsigned child_bounds(int b, int level, const int* __restrict__ sb, const int* __restrict__ se,
+                                        const int* __restrict__ tb, const int* __restrict__ te,
+                                        const unsigned long long* __restrict__ prefix,
+                                        const unsigned long long* __restrict__ skey,
+                                        const unsigned long long* __restrict__ tkey, int lane, int* s_lo, int* s_hi,
+                                        int* t_lo, int* t_hi) {
+  const int shift = 3 * (21 - (level + 1));
+  const unsigned long long p3 = prefix[b] << 3;
+  int v = 0;
+  if (lane <= 8) v = lower_bound_u64(skey, sb[b], se[b], (p3 + (unsigned long long)lane) << shift);
+  else if (lane >= 16 && lane <= 24) v = lower_bound_u64(tkey, tb[b], te[b], (p3 + (unsigned long long)(lane - 16)) << shift);
+  const int o = lane & 7;
+  *s_lo = __shfl_sync(0xffffffffu, v, o);
+  *s_hi = __shfl_sync(0xffffffffu, v, o + 1);
+  *t_lo = __shfl_sync(0xffffffffu, v, 16 + o);
+  *t_hi = __shfl_sync(0xffffffffu, v, 17 + o);
+  // bit o set: child octant o holds a source or a target
+  return __ballot_sync(0xffffffffu, lane < 8 && (*s_hi > *s_lo || *t_hi > *t_lo)) & 0xFFu;
+}
+
 __global__ void k_count_children(int lb, int le, int level, int leaf, const int* __restrict__ sb,
                                  const int* __restrict__ se, const int* __restrict__ tb,
                                  const int* __restrict__ te, const unsigned long long* __restrict__ prefix,
@@ -228,21 +253,16 @@ __global__ void k_count_children(int lb, int le, int level, int leaf, const int*
                                  const unsigned long long* __restrict__ tkey, int* __restrict__ nchild,
                                  const int* __restrict__ comp, const int* __restrict__ comp_kind,
                                  const int* __restrict__ coord, int split_iface) {
-  int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= le) return;
-  int ns = se[b] - sb[b], nt = te[b] - tb[b];
+  const int b = lb + (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= le) return;                       // whole warps leave together
+  const int ns = se[b] - sb[b], nt = te[b] - tb[b];
   int cnt = 0;
   if (refine_box(level, leaf, ns, nt, split_iface && comp_kind[comp[b]] == CK_REAC, coord[3 * b + 2])) {
-    int shift = 3 * (21 - (level + 1));
-    for (int o = 0; o < 8; ++o) {
-      unsigned long long cp = (prefix[b] << 3) | o;
-      unsigned long long k0 = cp << shift, k1 = (cp + 1) << shift;
-      int s0 = lower_bound_u64(skey, sb[b], se[b], k0), s1 = lower_bound_u64(skey, sb[b], se[b], k1);
-      int t0 = lower_bound_u64(tkey, tb[b], te[b], k0), t1 = lower_bound_u64(tkey, tb[b], te[b], k1);
-      if (s1 > s0 || t1 > t0) ++cnt;
-    }
+    int s0, s1, t0, t1;
+    cnt = __popc(child_bounds(b, level, sb, se, tb, te, prefix, skey, tkey, lane, &s0, &s1, &t0, &t1));
   }
-  nchild[b - lb] = cnt;
+  if (lane == 0) nchild[b - lb] = cnt;
 }
 
 __global__ void k_write_children(int lb, int le, int level, int nb_next_base, const int* __restrict__ scan,
@@ -253,31 +273,29 @@ __global__ void k_write_children(int lb, int le, int level, int nb_next_base, co
                                  int* __restrict__ nchild, int* __restrict__ coord,
                                  const unsigned long long* __restrict__ skey,
                                  const unsigned long long* __restrict__ tkey) {
-  int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = lb + (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (b >= le) return;
-  int n = nchild_lvl[b - lb];
-  int base = nb_next_base + scan[b - lb];
-  child0[b] = n ? base : -1;
-  nchild[b] = n;
+  const int n = nchild_lvl[b - lb];
+  const int base = nb_next_base + scan[b - lb];
+  if (lane == 0) {
+    child0[b] = n ? base : -1;
+    nchild[b] = n;
+  }
   if (!n) return;
-  int shift = 3 * (21 - (level + 1));
-  int k = 0;
-  for (int o = 0; o < 8; ++o) {
-    unsigned long long cp = (prefix[b] << 3) | o;
-    unsigned long long k0 = cp << shift, k1 = (cp + 1) << shift;
-    int s0 = lower_bound_u64(skey, sb[b], se[b], k0), s1 = lower_bound_u64(skey, sb[b], se[b], k1);
-    int t0 = lower_bound_u64(tkey, tb[b], te[b], k0), t1 = lower_bound_u64(tkey, tb[b], te[b], k1);
-    if (s1 > s0 || t1 > t0) {
-      int c = base + k++;
-      comp[c] = comp[b];
-      lev[c] = level + 1;
-      prefix[c] = cp;
-      sb[c] = s0; se[c] = s1; tb[c] = t0; te[c] = t1;
-      parent[c] = b;
-      coord[3 * c] = compact3(cp);
-      coord[3 * c + 1] = compact3(cp >> 1);
-      coord[3 * c + 2] = compact3(cp >> 2);
-    }
+  int s0, s1, t0, t1;
+  const unsigned mask = child_bounds(b, level, sb, se, tb, te, prefix, skey, tkey, lane, &s0, &s1, &t0, &t1);
+  if (lane < 8 && ((mask >> lane) & 1u)) {
+    const int c = base + __popc(mask & ((1u << lane) - 1u));
+    const unsigned long long cp = (prefix[b] << 3) | (unsigned long long)lane;
+    comp[c] = comp[b];
+    lev[c] = level + 1;
+    prefix[c] = cp;
+    sb[c] = s0; se[c] = s1; tb[c] = t0; te[c] = t1;
+    parent[c] = b;
+    coord[3 * c] = compact3(cp);
+    coord[3 * c + 1] = compact3(cp >> 1);
+    coord[3 * c + 2] = compact3(cp >> 2);
   }
 }
 
@@ -439,7 +457,18 @@ static T* need(DevBuf& b, size_t n) {
   return b.as<T>();
 }
 
-static void exclusive_scan(Workspace& ws, const int* in, int* out, int n, cudaStream_t st) {
+// off[k][b] = all[k nb + b] - all[k nb] for b <= nb (list k's CSR offsets
+// from the scan of the four lists' counts); tot[k] = off[k][nb]
+__global__ void k_list_offsets(int nb, const int* __restrict__ all, int* __restrict__ off, int* __restrict__ tot) {
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= 4 * ((long)nb + 1)) return;
+  const int k = (int)(e / (nb + 1)), b = (int)(e % (nb + 1));
+  const int v = all[(long)k * nb + b] - all[(long)k * nb];
+  off[e] = v;
+  if (b == nb) tot[k] = v;
+}
+
+static void exclusive_scan(Workspace& ws, const int* in, int* out, long n, cudaStream_t st) {
   dev_exclusive_scan(in, out, n, ws.sort_tmp, st);
 }
 
@@ -783,7 +812,7 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     if (n == 0) break;
     int* cntl = need<int>(ws.lvlcnt, n + 1);
     int* scn = need<int>(ws.lvlscan, n + 1);
-    LAUNCH(k_count_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, h->leaf, ws.bsb.as<int>(), ws.bse.as<int>(),
+    LAUNCH(k_count_children<<<(n + 3) / 4, 128, 0, st>>>(lb, le, level, h->leaf, ws.bsb.as<int>(), ws.bse.as<int>(),
                                                       ws.btb.as<int>(), ws.bte.as<int>(), ws.bprefix.as<unsigned long long>(),
                                                       skey, tkey, cntl, ws.bcomp.as<int>(), dkind, ws.bcoord.as<int>(),
                                                       (h->flags & FMM_TREE_COUNTS) ? 0 : 1));
@@ -794,7 +823,7 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
     FMM_CHECK(cudaStreamSynchronize(st));
     int total = last_cnt + last_scan;
     grow_boxes((size_t)le + total, (size_t)le);
-    LAUNCH(k_write_children<<<(n + 127) / 128, 128, 0, st>>>(lb, le, level, le, scn, cntl, ws.bcomp.as<int>(), ws.blevel.as<int>(),
+    LAUNCH(k_write_children<<<(n + 3) / 4, 128, 0, st>>>(lb, le, level, le, scn, cntl, ws.bcomp.as<int>(), ws.blevel.as<int>(),
                                                       ws.bprefix.as<unsigned long long>(), ws.bsb.as<int>(), ws.bse.as<int>(),
                                                       ws.btb.as<int>(), ws.bte.as<int>(), ws.bparent.as<int>(),
                                                       ws.bchild0.as<int>(), ws.bnchild.as<int>(), ws.bcoord.as<int>(), skey, tkey));
@@ -820,22 +849,16 @@ void build_trees(fmm_layered* h, long ns, const double* src, const double* q, lo
   LAUNCH(k_lists<false><<<(nb + 127) / 128, 128, 0, st>>>(nb, T, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                    nullptr, nullptr, flags));
   FMM_CHECK(cudaGetLastError());
+  // offsets of the four lists: one scan over the counts of all four
+  // (cnt[4][nb], then one zero), each list's offsets relative to its start
+  FMM_CHECK(cudaMemsetAsync(cnt + (size_t)4 * nb, 0, 4, st));
+  int* scanall = need<int>(ws.lvlscan, 4 * (size_t)nb + 8);
+  int* dtot = scanall + 4 * (size_t)nb + 1;
+  exclusive_scan(ws, cnt, scanall, 4 * (long)nb + 1, st);
+  LAUNCH(k_list_offsets<<<(unsigned)((4 * ((long)nb + 1) + 255) / 256), 256, 0, st>>>(nb, scanall, off, dtot));
   std::vector<int> tot(4);
-  for (int k = 0; k < 4; ++k) {
-    FMM_CHECK(cudaMemsetAsync(cnt + (size_t)4 * nb + k, 0, 4, st));
-  }
-  for (int k = 0; k < 4; ++k) {
-    // offsets over nb+1 entries: scan of (cnt[k][0..nb-1], 0)
-    int* c = cnt + (size_t)k * nb;
-    int* o = off + (size_t)k * (nb + 1);
-    exclusive_scan(ws, c, o, nb, st);
-    int lc = 0, ls = 0;
-    FMM_CHECK(cudaMemcpyAsync(&lc, c + nb - 1, 4, cudaMemcpyDeviceToHost, st));
-    FMM_CHECK(cudaMemcpyAsync(&ls, o + nb - 1, 4, cudaMemcpyDeviceToHost, st));
-    FMM_CHECK(cudaStreamSynchronize(st));
-    tot[k] = lc + ls;
-    FMM_CHECK(cudaMemcpyAsync(o + nb, &tot[k], 4, cudaMemcpyHostToDevice, st));
-  }
+  FMM_CHECK(cudaMemcpyAsync(tot.data(), dtot, 16, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaStreamSynchronize(st));
   int* vi = need<int>(ws.vi, tot[0]);
   int* ui = need<int>(ws.ui, tot[1]);
   int* wi = need<int>(ws.wi, tot[2]);
