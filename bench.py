@@ -170,12 +170,15 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def timed_evals(torch, solver, src, q, tgt, out, steps, warmup, flush, stream):
+def timed_evals(torch, solver, src, q, tgt, out, steps, warmup, flush, stream, nvtx=None):
     """Warm-up, then `steps` evaluations each timed with CUDA events on the
-    evaluation stream, the L2 flushed before each; returns (ms list, stats)."""
+    evaluation stream, the L2 flushed before each; returns (ms list, stats).
+    `nvtx` names a range around the timed evaluations (for a profiler)."""
     for _ in range(max(3, warmup)):
         solver.eval(src, q, tgt, out=out)
     ms, stats = [], []
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     for _ in range(steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -186,6 +189,8 @@ def timed_evals(torch, solver, src, q, tgt, out, steps, warmup, flush, stream):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         stats.append(solver.stats())
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     return ms, stats
 
 
@@ -263,9 +268,8 @@ def mixed_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws):
     n = len(w["tgt"])
     mixed = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], mixed=True)
     out_m = torch.empty_like(ref_out)
-    torch.cuda.nvtx.range_push("timed_mixed")
-    mms, mst = timed_evals(torch, mixed, src, q, tgt, out_m, args.steps, args.warmup, flush, stream)
-    torch.cuda.nvtx.range_pop()
+    mms, mst = timed_evals(torch, mixed, src, q, tgt, out_m, args.steps, args.warmup, flush, stream,
+                           nvtx="timed_mixed")
     mixed.close()
     m_ms = statistics.mean(mms)
     tc_ms = statistics.mean(s["gpu_ms_m2l_gemm"] for s in mst)
@@ -310,12 +314,11 @@ def surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, 
                              surrogate=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    err, ok = ms_surr.train_surrogate(**box, samples=131072, steps=8000, bound=1e-5, seed=5)
+    err, ok = ms_surr.train_surrogate(**box, samples=262144, steps=8000, bound=1e-5, seed=5)
     train_s = time.perf_counter() - t0
     judged = err[err >= 0]
-    torch.cuda.nvtx.range_push("timed_mixed_surrogate")
-    sms, sst = timed_evals(torch, ms_surr, src, q, tgt, out, args.steps, args.warmup, flush, stream)
-    torch.cuda.nvtx.range_pop()
+    sms, sst = timed_evals(torch, ms_surr, src, q, tgt, out, args.steps, args.warmup, flush, stream,
+                           nvtx="timed_mixed_surrogate")
     ms_surr.close()
     st_s = sst[-1]
     res = {
@@ -324,7 +327,7 @@ def surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, 
                             "near_reac_ms": statistics.mean(s["gpu_ms_near_reac"] for s in qst),
                             "n_reac_pairs": st_q["n_reac_pairs"], "n_reac_nodes": st_q["n_reac_nodes"],
                             "rel_l2_vs_fp64_path": _rel(out_q.cpu().numpy(), ref_out.cpu().numpy())},
-        "training": {"box": box, "samples_per_component": 131072, "steps": 8000, "train_s": train_s,
+        "training": {"box": box, "samples_per_component": 262144, "steps": 8000, "train_s": train_s,
                      "components": int((err >= 0).any(axis=1).sum()),
                      "heldout_rel_rms_median": float(np.median(judged)), "heldout_rel_rms_max": float(judged.max()),
                      "cells_within_1e-5": int(ok.sum()), "cells": int(judged.size)},

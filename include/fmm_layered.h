@@ -54,7 +54,10 @@ extern "C" {
                                  hi/lo split operands with power-of-two
                                  scaling, FP32 accumulation (3 products);
                                  free-space near field in FP32 with a
-                                 compensated sum; expansions, operators, the
+                                 compensated sum; in the reaction near field
+                                 the real-axis tail of the Sommerfeld
+                                 quadrature in FP32 with a compensated sum;
+                                 expansions, operators, the rest of the
                                  reaction near field and all sums over
                                  translations stay FP64.  Relative error of
                                  the potentials below 1e-5.                    */
@@ -203,10 +206,10 @@ int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const long* n_src,
  * Learned surrogate of the reaction components (the form that replaces the
  * Sommerfeld quadrature of eq. generalcomponentsimag in the near field).
  * For every reaction component (l, l', a, b) of the medium, draws
- * samples_per_component points (rounded up to a multiple of 64) uniformly in
+ * samples_per_component points (rounded up to a multiple of 512) uniformly in
  * the box rho in [0, rho_max], zt, zs in [z_min, z_max] (zt: target distance
  * to the component's reference interface, zs: image depth), stratified over
- * the cells of a 4 x 4 x 4 grid, plus 1/8 as many held-out points (seeded
+ * the cells of an 8 x 8 x 8 grid, plus 1/8 as many held-out points (seeded
  * counter-based generator), evaluates the component there with the
  * library's quadrature, and trains one network per component on
  * y = 4 pi R u, R = sqrt(rho^2 + (zt + zs)^2): hidden layers 3 -> 64 -> 64 ->
@@ -230,10 +233,10 @@ int fmm_layered_surrogate_train(fmm_layered_t* h, double rho_max, double z_min,
  * retraining; synchronous).  FMM_ERR_ARG if untrained or bound <= 0. */
 int fmm_layered_surrogate_set_bound(fmm_layered_t* h, double bound);
 
-/* Held-out verdict of the last training: cell_err[slot * 64 + cell] (relative
+/* Held-out verdict of the last training: cell_err[slot * 512 + cell] (relative
  * RMS error, -1 where not judged) and cell_ok (1 where used), slot =
- * ((l (L+1) + l') 2 + a) 2 + b, cell = (c_rho 4 + c_zt) 4 + c_zs; arrays of
- * 4 (L+1)^2 64 entries (host, either may be NULL).  FMM_ERR_ARG if untrained. */
+ * ((l (L+1) + l') 2 + a) 2 + b, cell = (c_rho 8 + c_zt) 8 + c_zs; arrays of
+ * 4 (L+1)^2 512 entries (host, either may be NULL).  FMM_ERR_ARG if untrained. */
 int fmm_layered_surrogate_report(const fmm_layered_t* h, double* cell_err,
                                  unsigned char* cell_ok);
 

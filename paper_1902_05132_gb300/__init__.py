@@ -21,6 +21,7 @@ FMM_NORM_PAPER = 1
 FMM_MIXED = 2
 FMM_SURROGATE = 4
 FMM_TREE_COUNTS = 8
+SURR_CELLS = 512          # cells of the surrogate's held-out check (8 x 8 x 8)
 FMM_TEST_STALL_TC = 1 << 30
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "point on an interface", -3: "non-finite input",
@@ -258,12 +259,13 @@ class LayeredFMM:
         return self.surrogate_report()
 
     def surrogate_report(self):
-        """(cell_err, cell_ok), shape [4 L1^2, 64]; slot ((l*L1 + l')*2 + a)*2 + b."""
-        n = 4 * len(self.k) ** 2 * 64
+        """(cell_err, cell_ok), shape [4 L1^2, 512]; slot ((l*L1 + l')*2 + a)*2 + b,
+        cell (c_rho*8 + c_zt)*8 + c_zs."""
+        n = 4 * len(self.k) ** 2 * SURR_CELLS
         err = np.zeros(n, dtype=np.float64)
         ok = np.zeros(n, dtype=np.uint8)
         self._check(lib().fmm_layered_surrogate_report(self.h, _ptr(err), _ptr(ok)))
-        return err.reshape(-1, 64), ok.reshape(-1, 64).astype(bool)
+        return err.reshape(-1, SURR_CELLS), ok.reshape(-1, SURR_CELLS).astype(bool)
 
     def set_components(self, first=0, count=-1):
         """Evaluate only components [first, first + count) (count < 0: all)."""

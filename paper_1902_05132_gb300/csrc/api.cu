@@ -1,5 +1,6 @@
 // C ABI and host orchestration of one evaluation (Algorithm 1 for every
 // component, summed as in eq. totalinteraction).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -331,7 +332,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   launch_mark_reac(nb, B, dcg, loff, ws.vi.as<int>(), dused, err, st);
   FMM_CHECK(cudaGetLastError());
   // host copies needed for scheduling
-  std::vector<int> bcomp(nb), bnchild(nb), bsb(nb), bse(nb), btb(nb), bte(nb);
+  std::vector<int> bcomp(nb), bnchild(nb), bsb(nb), bse(nb), btb(nb), bte(nb), bpar(nb);
   std::vector<unsigned char> used((size_t)nc * 23 * 40);
   FMM_CHECK(cudaMemcpyAsync(bcomp.data(), ws.bcomp.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaMemcpyAsync(bnchild.data(), ws.bnchild.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
@@ -339,6 +340,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaMemcpyAsync(bse.data(), ws.bse.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaMemcpyAsync(btb.data(), ws.btb.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaMemcpyAsync(bte.data(), ws.bte.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(bpar.data(), ws.bparent.ptr, 4 * nb, cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaMemcpyAsync(used.data(), dused, used.size(), cudaMemcpyDeviceToHost, st));
   std::vector<int> lo_all(4 * (size_t)(nb + 1));
   FMM_CHECK(cudaMemcpyAsync(lo_all.data(), ws.loff.ptr, 4 * lo_all.size(), cudaMemcpyDeviceToHost, st));
@@ -549,7 +551,6 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     d_rot_tab = (long*)tc_need(ws.rot_tab, sizeof(long) * m2m_az.size() + 64);
     FMM_CHECK(cudaMemcpyAsync(d_rot_tab, m2m_az.data(), sizeof(long) * m2m_az.size(), cudaMemcpyHostToDevice, st));
   }
-  E.mark(2, st);
   // ---- passes
   auto t2 = Clock::now();
   long* dtabs = nullptr;
@@ -579,14 +580,48 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
         if (l >= 2) l2p_leaves.push_back(b);
       }
     }
+  // near-field leaves with the most pairs first (targets x U and W entries),
+  // so that the long CTAs start in the first wave; each CTA sums only its own
+  // targets, so the order does not change any result
+  {
+    const int* uo_h = lo_all.data() + (nb + 1);
+    const int* wo_h = lo_all.data() + 2 * (size_t)(nb + 1);
+    auto work = [&](int b) {
+      return (long)(bte[b] - btb[b]) * (long)(uo_h[b + 1] - uo_h[b] + wo_h[b + 1] - wo_h[b] + 1);
+    };
+    auto by_work = [&](int a, int b) {
+      const long wa = work(a), wb = work(b);
+      return wa != wb ? wa > wb : a < b;
+    };
+    std::sort(near_free.begin(), near_free.end(), by_work);
+    std::sort(near_reac.begin(), near_reac.end(), by_work);
+  }
+  // reaction near field: (leaf, first target) items of up to 4 targets, for
+  // the leaves with U, W or X entries (their own or an ancestor's X list)
+  std::vector<int> reac_items;
+  {
+    const int* uo_h = lo_all.data() + (nb + 1);
+    const int* wo_h = lo_all.data() + 2 * (size_t)(nb + 1);
+    const int* xo_h = lo_all.data() + 3 * (size_t)(nb + 1);
+    for (int b : near_reac) {
+      bool any = uo_h[b + 1] > uo_h[b] || wo_h[b + 1] > wo_h[b];
+      for (int A = b; !any && A >= 0; A = bpar[A]) any = xo_h[A + 1] > xo_h[A];
+      if (!any) continue;
+      for (int t = btb[b]; t < bte[b]; t += 4) {
+        reac_items.push_back(b);
+        reac_items.push_back(t);
+      }
+    }
+  }
   std::vector<int> sched;
   auto push = [&](const std::vector<int>& v) { long o = sched.size(); sched.insert(sched.end(), v.begin(), v.end()); return o; };
   long o_p2m = push(p2m_leaves), o_l2p = push(l2p_leaves), o_near_free = push(near_free),
-       o_near_reac = push(near_reac);
+       o_near_reac = push(reac_items);
   std::vector<long> o_m2m(23), o_m2l(23);
   for (int l = 0; l <= maxlev; ++l) { o_m2m[l] = push(m2m_lvl[l]); o_m2l[l] = push(m2l_lvl[l]); }
   int* dsched = upload(ws.lcnt, sched, st);
   FMM_CHECK(cudaMemsetAsync(err, 0, 4, st));
+  E.mark(2, st);        // the scheduling above is host work: it counts to the operator stage
   // upward pass
   launch_p2m(p, dsched + o_p2m, (int)p2m_leaves.size(), B, dcg, ws.spos.as<double>(), ws.sq.as<cplx>(), M, st);
   for (int l = maxlev; l >= 2; --l) {
@@ -645,7 +680,8 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   E.mark(6, st);
   RuleView rv_reac = make_rule_view(h->rule, coef);
   rv_reac.surr = surrogate_view(h);
-  launch_near_reac(dsched + o_near_reac, (int)near_reac.size(), NB, dnc, rv_reac, ws.spos.as<double>(),
+  rv_reac.tail_f32 = (h->flags & FMM_MIXED) ? 1 : 0;
+  launch_near_reac(dsched + o_near_reac, (int)(reac_items.size() / 2), NB, dnc, rv_reac, ws.spos.as<double>(),
                    ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 3, counters + 6, st);
   FMM_CHECK(cudaGetLastError());
   E.mark(7, st);

@@ -281,6 +281,7 @@ struct RuleView {
   int Q, n_near, per_panel, n_panels;
   double ta, panel;
   SurrView surr;           // learned surrogate of the reaction components (w == nullptr: none)
+  int tail_f32;            // reaction near field: real-axis tail in FP32 (mixed form)
 };
 struct NearComp { int kind, l, lp, a, b; double k; double dref; long coef_off; };
 struct NearBoxes {

@@ -390,33 +390,29 @@ __device__ inline void warp_sum(cplx& v) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leaves, NearBoxes B,
+// Work items: (leaf, first target) pairs, up to 4 targets each (one per
+// warp), so that the targets with the costliest pairs (those next to the
+// interface, where the quadrature takes the most nodes) spread over many
+// CTAs; only leaves with near-field entries get items.
+__global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ items, NearBoxes B,
                                                    const NearComp* __restrict__ ncs, RuleView R,
                                                    const double* __restrict__ spos, const cplx* __restrict__ sq,
                                                    const double* __restrict__ tpos, cplx* __restrict__ phi,
                                                    unsigned long long* __restrict__ counters,
                                                    unsigned long long* __restrict__ box) {
-  const int T = leaves[blockIdx.x];
+  const int T = items[2 * blockIdx.x], t_first = items[2 * blockIdx.x + 1];
+  const int t_end = min(B.te[T], t_first + 4);
   const NearComp nc = ncs[B.comp[T]];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = (int)(nc.coef_off / R.Q);
-  // leaves without near-field entries (the usual case with the interface
-  // rule of the reaction trees) leave at once
-  __shared__ int s_any;
-  if (threadIdx.x == 0) {
-    int any = (B.uo[T + 1] > B.uo[T]) || (B.wo[T + 1] > B.wo[T]);
-    for (int A = T; !any && A >= 0; A = B.parent[A]) any = B.xo[A + 1] > B.xo[A];
-    s_any = any;
-  }
-  __syncthreads();
-  if (!s_any) return;
-  // the component's network, summed to FP32, in shared memory (only when a
-  // surrogate is attached: the launch then gives SURR_NINF floats)
+  // the hidden layers of the component's network, summed to FP32, in shared
+  // memory (only when a surrogate is attached: the launch then gives
+  // SURR_NTRUNK floats); the cell output layers stay in global memory
   extern __shared__ float s_net[];
-  if (R.surr.w) {
-    const __nv_bfloat16* hi = R.surr.w + (long)slot * 2 * SURR_NINF;
-    for (int i = threadIdx.x; i < SURR_NINF; i += blockDim.x)
-      s_net[i] = __bfloat162float(hi[i]) + __bfloat162float(hi[SURR_NINF + i]);
+  const __nv_bfloat16* net = R.surr.w ? R.surr.w + (long)slot * 2 * SURR_NINF : nullptr;
+  if (net) {
+    for (int i = threadIdx.x; i < SURR_NTRUNK; i += blockDim.x)
+      s_net[i] = __bfloat162float(net[i]) + __bfloat162float(net[SURR_NINF + i]);
     __syncthreads();
   }
   const cplx* coef = R.coef + nc.coef_off;
@@ -424,7 +420,7 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leave
   const cplx* kzp = R.kz + (long)nc.lp * R.Q;
   unsigned long long my_pairs = 0, my_nodes = 0, my_surr = 0;
   double rho_hi = 0.0, z_lo = INFINITY, z_hi = 0.0;
-  for (int t = B.tb[T] + warp; t < B.te[T]; t += 4) {
+  for (int t = t_first + warp; t < t_end; t += 4) {
     const double x = tpos[3 * t], y = tpos[3 * t + 1];
     const double zt = fabs(tpos[3 * t + 2] - nc.dref);
     cplx acc = C(0, 0);
@@ -462,7 +458,7 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leave
             float xin[3];
             int cell;
             if (surr_inputs(R.surr, rho, zt, zs, xin, &cell) && R.surr.ok[slot * SURR_CELLS + cell]) {
-              const float2 v = surr_forward_f32(s_net, xin, cell);
+              const float2 v = surr_forward_f32(s_net, net, xin, cell);
               const double f = 1.0 / (4.0 * FMM_PI * sqrt(rho * rho + (zt + zs) * (zt + zs)));
               cfma(acc, C((double)v.x * f, (double)v.y * f), qs);
               by_net = true;
@@ -484,9 +480,24 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ leave
             cfma(part, cmul(J, ex), coef[qn]);
           }
           double tail = 0.0;
-          for (int qn = R.n_near + lane; qn < nq; qn += 32) {
-            const double tq = R.kr[qn].x;
-            tail += coef[qn].x * j0(tq * rj) * exp(-(kzl[qn].y * zt + kzp[qn].y * zsj));
+          if (R.tail_f32) {
+            // mixed form: the real tail (every factor real, the integrand a
+            // decaying, oscillating sum) in FP32 with a compensated sum
+            const float rf = (float)rj, ztf = (float)zt, zsf = (float)zsj;
+            float sum = 0.0f, cmp = 0.0f;
+            for (int qn = R.n_near + lane; qn < nq; qn += 32) {
+              const float term = (float)coef[qn].x * j0f((float)R.kr[qn].x * rf) *
+                                 expf(-((float)kzl[qn].y * ztf + (float)kzp[qn].y * zsf));
+              const float y = term - cmp, tt = sum + y;
+              cmp = (tt - sum) - y;
+              sum = tt;
+            }
+            tail = (double)sum - (double)cmp;
+          } else {
+            for (int qn = R.n_near + lane; qn < nq; qn += 32) {
+              const double tq = R.kr[qn].x;
+              tail += coef[qn].x * j0(tq * rj) * exp(-(kzl[qn].y * zt + kzp[qn].y * zsj));
+            }
           }
           part.x += tail;
           cfma(acc, part, qj);
@@ -643,6 +654,7 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
   v.ta = R.ta;
   v.panel = R.panel;
   v.surr = SurrView{};
+  v.tail_f32 = 0;
   return v;
 }
 
@@ -657,9 +669,10 @@ __global__ void k_surr_samples(long n, long nper, const int* __restrict__ slots,
   const int slot = slots[e / nper];
   const int lp = (slot >> 2) % L1, l = (slot >> 2) / L1;      // slot = ((l L1 + l') 2 + a) 2 + b
   const int cell = (int)((e % nper) / (nper / SURR_CELLS));
-  const int c0 = cell >> 4, c1 = (cell >> 2) & 3, c2 = cell & 3;
-  double u0 = (c0 + surr_uniform(seed, 3 * e)) * 0.25, u1 = (c1 + surr_uniform(seed, 3 * e + 1)) * 0.25,
-         u2 = (c2 + surr_uniform(seed, 3 * e + 2)) * 0.25;
+  const int c0 = cell / (SURR_GRID * SURR_GRID), c1 = (cell / SURR_GRID) % SURR_GRID, c2 = cell % SURR_GRID;
+  const double inv = 1.0 / SURR_GRID;
+  double u0 = (c0 + surr_uniform(seed, 3 * e)) * inv, u1 = (c1 + surr_uniform(seed, 3 * e + 1)) * inv,
+         u2 = (c2 + surr_uniform(seed, 3 * e + 2)) * inv;
   double rho = u0 * box.rho_max;
   double zt = box.z_min + u1 * (box.z_max - box.z_min), zs = box.z_min + u2 * (box.z_max - box.z_min);
   cplx u = reac_pair(R, R.coef + (long)slot * R.Q, R.kz + (long)l * R.Q, R.kz + (long)lp * R.Q, rho, zt, zs);
@@ -676,15 +689,12 @@ void launch_surr_samples(long n, long nper, const int* slots, int L1, SurrView b
   if (n) LAUNCH(k_surr_samples<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, nper, slots, L1, box, R, seed, X, Y));
 }
 
-void launch_near_reac(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
+void launch_near_reac(const int* items, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,
                       const cplx* sq, const double* tpos, cplx* phi, unsigned long long* counters,
                       unsigned long long* box, cudaStream_t st) {
   if (!n) return;
-  const size_t smem = R.surr.w ? sizeof(float) * SURR_NINF : 0;
-  // the network takes more than the default 48 KB (set per call: per device, cheap)
-  FMM_CHECK(cudaFuncSetAttribute(k_near_reac, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(float) * SURR_NINF)));
-  LAUNCH(k_near_reac<<<n, 128, smem, st>>>(leaves, B, ncs, R, spos, sq, tpos, phi, counters, box));
+  const size_t smem = R.surr.w ? sizeof(float) * SURR_NTRUNK : 0;
+  LAUNCH(k_near_reac<<<n, 128, smem, st>>>(items, B, ncs, R, spos, sq, tpos, phi, counters, box));
 }
 
 void launch_near(const int* leaves, int n, NearBoxes B, const NearComp* ncs, RuleView R, const double* spos,

@@ -4,7 +4,7 @@
 //
 // Data: for every reaction component of the medium, points drawn uniformly in
 // the box [0, rho_max] x [z_min, z_max]^2 of (rho, zt, zs), stratified by the
-// cells of a 4 x 4 x 4 grid, with the values of the component computed by the
+// cells of an 8 x 8 x 8 grid, with the values of the component computed by the
 // library's quadrature (the plain path of the near field, eq.
 // generalcomponentsimag), plus an independent held-out set.
 // Training, in three steps:
@@ -297,8 +297,8 @@ __global__ void k_surr_heldout(long n, long nper, const int* __restrict__ slots,
   const int si = (int)(e / nper);
   float x[3] = {X[3 * e], X[3 * e + 1], X[3 * e + 2]};
   int c[3];
-  for (int i = 0; i < 3; ++i) c[i] = min(3, max(0, (int)((x[i] + 1.0f) * 2.0f)));
-  int cell = (c[0] * 4 + c[1]) * 4 + c[2];
+  for (int i = 0; i < 3; ++i) c[i] = min(SURR_GRID - 1, max(0, (int)((x[i] + 1.0f) * (0.5f * SURR_GRID))));
+  int cell = (c[0] * SURR_GRID + c[1]) * SURR_GRID + c[2];
   float2 o = surr_forward(winf + (long)slots[si] * 2 * SURR_NINF, x, cell);
   float y0 = Y[2 * e], y1 = Y[2 * e + 1];
   double* a = acc + ((long)si * SURR_CELLS + cell) * 3;

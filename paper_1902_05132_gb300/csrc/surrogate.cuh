@@ -7,7 +7,7 @@
 // box-normalized inputs to y = 4 pi R u, R = sqrt(rho^2 + (zt + zs)^2) the
 // distance to the image point, which removes the 1/R decay and leaves an
 // O(1) smooth function.  Architecture: 3 -> 64 -> 64 -> 64 (GELU), then a
-// linear output layer 64 -> 2 (Re, Im) chosen by the cell of a 4 x 4 x 4 grid
+// linear output layer 64 -> 2 (Re, Im) chosen by the cell of an 8 x 8 x 8 grid
 // over the input box.
 //  * Training: the three hidden layers and a shared output layer by Adam on
 //    the standardized outputs (weights and layer inputs rounded to BF16, FP32
@@ -23,7 +23,8 @@
 
 #define SURR_H 64
 #define SURR_NPAR (SURR_H * 3 + SURR_H + SURR_H * SURR_H + SURR_H + SURR_H * SURR_H + SURR_H + 2 * SURR_H + 2)
-#define SURR_CELLS 64
+#define SURR_GRID 8                    // cells per input axis
+#define SURR_CELLS (SURR_GRID * SURR_GRID * SURR_GRID)
 // parameter offsets: W1 [64][3], b1, W2 [64][64], b2, W3 [64][64], b3, W4 [2][64], b4
 #define SURR_W1 0
 #define SURR_B1 (SURR_W1 + SURR_H * 3)
@@ -75,8 +76,9 @@ __device__ inline bool surr_inputs(const SurrView& S, double rho, double zt, dou
   x[0] = (float)(2.0 * u0 - 1.0);
   x[1] = (float)(2.0 * u1 - 1.0);
   x[2] = (float)(2.0 * u2 - 1.0);
-  int c0 = min(3, (int)(u0 * 4.0)), c1 = min(3, (int)(u1 * 4.0)), c2 = min(3, (int)(u2 * 4.0));
-  *cell = (c0 * 4 + c1) * 4 + c2;
+  const int g = SURR_GRID;
+  int c0 = min(g - 1, (int)(u0 * g)), c1 = min(g - 1, (int)(u1 * g)), c2 = min(g - 1, (int)(u2 * g));
+  *cell = (c0 * g + c1) * g + c2;
   return true;
 }
 
@@ -120,12 +122,14 @@ __device__ inline void surr_features(const __nv_bfloat16* __restrict__ hi, const
   for (int j = 0; j < SURR_H; ++j) f[j] = a[j];
 }
 
-// The same forward pass with the parameters already summed to FP32 (hi + lo,
-// exact) and laid out as in the inference parameters (hidden layers, then
-// the cell output layers), e.g. staged in shared memory.  Same operations in
-// the same order as surr_features + the output layer below: bit-identical
-// results.  Fully unrolled so that the layer activations stay in registers.
-__device__ __forceinline__ float2 surr_forward_f32(const float* __restrict__ w, const float* x, int cell) {
+// The same forward pass with the hidden layers already summed to FP32 (hi +
+// lo, exact) and laid out as in the inference parameters (e.g. staged in
+// shared memory); the cell's output layer is read from the component's
+// inference parameters `W` (hi and lo parts).  Same operations in the same
+// order as surr_forward: bit-identical results.  Fully unrolled so that the
+// layer activations stay in registers.
+__device__ __forceinline__ float2 surr_forward_f32(const float* __restrict__ w, const __nv_bfloat16* __restrict__ W,
+                                                   const float* x, int cell) {
   float a[SURR_H], f[SURR_H];
   const float xi0 = surr_hilo(x[0]), xi1 = surr_hilo(x[1]), xi2 = surr_hilo(x[2]);
 #pragma unroll
@@ -164,13 +168,15 @@ __device__ __forceinline__ float2 surr_forward_f32(const float* __restrict__ w, 
     }
     a[j] = surr_hilo(surr_gelu(s));
   }
+  const __nv_bfloat16* hi = W;
+  const __nv_bfloat16* lo = W + SURR_NINF;
   float o[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float* r = w + SURR_NTRUNK + (cell * 2 + k) * SURR_HEAD_N;
-    float s = r[SURR_H];
+    const int r = SURR_NTRUNK + (cell * 2 + k) * SURR_HEAD_N;
+    float s = surr_w(hi, lo, r + SURR_H);
 #pragma unroll
-    for (int i = 0; i < SURR_H; ++i) s = fmaf(r[i], a[i], s);
+    for (int i = 0; i < SURR_H; ++i) s = fmaf(surr_w(hi, lo, r + i), a[i], s);
     o[k] = s;
   }
   return make_float2(o[0], o[1]);

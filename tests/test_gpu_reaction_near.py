@@ -83,7 +83,7 @@ def test_surrogate_in_the_fmm_near_field():
     box = dict(rho_max=1.001 * st_q["reac_near_rho_max"], z_min=0.999 * st_q["reac_near_z_min"],
                z_max=1.001 * st_q["reac_near_z_max"])
     assert 0 < box["z_min"] < box["z_max"] and box["rho_max"] > 0, box
-    err, ok = surr.train_surrogate(**box, samples=65536, steps=4000, bound=1e-5, seed=3)
+    err, ok = surr.train_surrogate(**box, samples=262144, steps=4000, bound=1e-5, seed=3)
     judged = err[err >= 0]
     got_s = surr.eval(src, q, tgt).cpu().numpy()
     surr.eval(src, q, tgt)

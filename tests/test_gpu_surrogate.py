@@ -28,7 +28,7 @@ def test_surrogate_report_and_strict_bound():
     import paper_1902_05132_gb300 as pkg
     w = workloads.two_layer(n=400)
     plain, surr = _solvers(pkg, w)
-    err, ok = surr.train_surrogate(**BOX, samples=16384, steps=1500, bound=1e-5, seed=1)
+    err, ok = surr.train_surrogate(**BOX, samples=131072, steps=1500, bound=1e-5, seed=1)
     # two layers: components (0,0,up,up), (0,1,up,down), (1,0,down,up), (1,1,down,down)
     L1 = 2
     slots = [((l * L1 + lp) * 2 + a) * 2 + b for l in range(2) for lp in range(2) for a in range(2) for b in range(2)
@@ -54,7 +54,7 @@ def test_surrogate_loose_bound_error_within_bound():
     w = workloads.two_layer(n=400)
     plain, surr = _solvers(pkg, w)
     bound = 3e-2
-    err, ok = surr.train_surrogate(**BOX, samples=16384, steps=1500, bound=bound, seed=2)
+    err, ok = surr.train_surrogate(**BOX, samples=131072, steps=1500, bound=bound, seed=2)
     assert ok.sum() > 0
     assert (err[ok] <= bound).all()
     src, q, tgt = to_dev(torch, w)

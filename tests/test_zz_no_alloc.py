@@ -41,7 +41,7 @@ def test_noalloc_uses_the_trained_surrogate_like_direct():
     import paper_1902_05132_gb300 as pkg
     w = workloads.two_layer(n=200, seed=6)
     s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=4, leaf=16, surrogate=True)
-    s.train_surrogate(rho_max=2.9, z_min=0.09, z_max=1.11, samples=4096, steps=300, bound=1e-5)
+    s.train_surrogate(rho_max=2.9, z_min=0.09, z_max=1.11, samples=65536, steps=300, bound=1e-5)
     _, ok = s.surrogate_set_bound(10.0)          # every judged cell uses the network
     assert ok.sum() > 0
     plain = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=4, leaf=16)
