@@ -9,7 +9,7 @@ handle's per-geometry cache, upward and downward passes, near field, sum),
 inputs resident in device memory.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-large] [--no-surrogate] [--no-cpu-baseline]
+                  [--no-large] [--no-surrogate] [--no-tables] [--no-cpu-baseline]
 
 Extra keys of the JSON line:
   mixed      the same workload in the mixed-precision form (FMM_MIXED)
@@ -18,6 +18,9 @@ Extra keys of the JSON line:
              near field, then the mixed + surrogate form (FMM_MIXED |
              FMM_SURROGATE) with the network trained on the near-field box
   large      N = 2^20, p = 10, complex charges: FP64 and mixed forms
+  tables     the reaction M2L from tabulated integrals (FMM_TABLES): table
+             build at create, evaluations with a new geometry every step
+             with and without the tables, error against the oracle values
   paper_table  the paper's timing study (Sec. 4, Table 1): irregular domains,
              p = 4, N = 618,256 .. 2,861,288; all components, the 3
              free-space ones and the 3 reaction ones the table selects
@@ -390,6 +393,61 @@ def large_leg(pkg, torch, dev, args, flush, stream, gold):
 PAPER_TABLE_36 = {618256: (2.29, 2.74), 1128556: (5.00, 3.21), 1862568: (11.45, 3.59), 2861288: (12.60, 3.90)}
 
 
+def tables_leg(pkg, torch, w, src, q, tgt, out, args, flush, stream, gold):
+    """Tabulated reaction M2L integrals (FMM_TABLES, Sec. 3.5): table build at
+    create, then evaluations whose geometry changes every step (all points
+    moved by a few 1e-4 along a fixed random direction field, so every box
+    width and hence every translation operator is new), with and without
+    the tables; the error of the tables path against the stored oracle values."""
+    rng = np.random.default_rng(7)
+    field = torch.tensor(rng.uniform(-1.0, 1.0, size=tuple(src.shape)), device=src.device)
+    field[:, 2] *= 0.5
+    t0 = time.perf_counter()
+    tab = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tables=True)
+    create_s = time.perf_counter() - t0
+    st0 = tab.stats()
+    res = {"create_s": create_s, "build_ms": st0["ms_tables"], "table_bytes": st0["table_bytes"]}
+    tab.eval(src, q, tgt, out=out)
+    if gold is not None:
+        res["rel_l2_vs_oracle_direct_2000"] = _rel(out.cpu().numpy()[gold["three_layer_sel2000"]],
+                                                   gold["three_layer_direct2000"])
+        res["rel_l2_vs_oracle_fmm_200"] = _rel(out.cpu().numpy()[gold["three_layer_fmm_sel"]],
+                                               gold["three_layer_fmm200"])
+
+    def moving(solver, steps, j0):
+        ms, stats = [], []
+        for j in range(steps):
+            s_j = src + (j0 + j + 1) * 2e-4 * field
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.eval(s_j, q, s_j, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(solver.stats())
+        return ms, stats
+
+    n = len(w["tgt"])
+    ms, stats = moving(tab, max(3, args.steps), 0)
+    res["moving_geometry"] = {
+        "value": n / (statistics.mean(ms) * 1e-3), "unit": "particles/s", "ms_per_step": statistics.mean(ms),
+        "operators_ms": statistics.mean(s["gpu_ms_operators"] for s in stats),
+        "table_classes_per_step": stats[-1]["n_reac_table_classes"],
+        "quadrature_nodes": stats[-1]["n_reac_T_nodes"]}
+    tab.close()
+    quad = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
+    quad.eval(src, q, tgt, out=out)
+    msq, statsq = moving(quad, 2, 100)
+    res["moving_geometry_quadrature"] = {
+        "value": n / (statistics.mean(msq) * 1e-3), "unit": "particles/s", "ms_per_step": statistics.mean(msq),
+        "operators_ms": statistics.mean(s["gpu_ms_operators"] for s in statsq),
+        "reaction_classes_per_step": statsq[-1]["n_reac_classes"]}
+    quad.close()
+    return res
+
+
 def paper_table_leg(pkg, torch, dev, flush, stream):
     """The paper's timing study (Sec. 4, Table 1) on its own workload: the
     irregular domains of workloads.paper_domains scaled to the table's N,
@@ -437,6 +495,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-paper-table", action="store_true")
+    ap.add_argument("--no-tables", action="store_true")
     ap.add_argument("--workload", default="three-layer-32768", choices=sorted(WORKLOADS))
     ap.add_argument("--split", default="problems", choices=["problems", "components"])
     args = ap.parse_args()
@@ -606,6 +665,8 @@ def main():
     if gold is not None:
         result["errors"]["mixed_vs_oracle_direct_2000"] = _rel(out_m.cpu().numpy()[gold["three_layer_sel2000"]],
                                                                gold["three_layer_direct2000"])
+    if not args.no_tables and ws == 1:
+        result["tables"] = tables_leg(pkg, torch, w, src, q, tgt, torch.empty_like(out), args, flush, stream, gold)
     if not args.no_surrogate:
         result["surrogate"] = surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, gold)
     if not args.no_large and ws == 1:

@@ -77,6 +77,21 @@ extern "C" {
                                  and X lists and those pairs are evaluated
                                  directly (Sommerfeld quadrature of eq.
                                  generalcomponentsimag, or the surrogate)    */
+#define FMM_TABLES      16u   /* reaction M2L operators from tabulated
+                                 Sommerfeld integrals (Sec. 3.5, eqs.
+                                 M2Ltable, metoletableform): at create, the
+                                 integrals S_{q,t,mu,nu} of every reaction
+                                 component are computed on the 40 rays of
+                                 M2L classes (box centres (jt + 1/2) w and
+                                 (js + 1/2) w from the interface, jt, js in
+                                 {0, 1}, horizontal offset w sqrt(dx^2+dy^2))
+                                 for k_max w in [2^-8, 2^1.5] and kept at 12
+                                 Chebyshev points per panel of log2(k_max w);
+                                 an evaluation interpolates them instead of
+                                 integrating, so a new geometry costs no
+                                 quadrature.  Classes outside that range use
+                                 the quadrature.  p <= 12 (FMM_ERR_UNSUPPORTED
+                                 otherwise); create then takes about a second */
 #define FMM_TEST_STALL_TC (1u << 30) /* test only, with FMM_MIXED: every
                                  stage of the tensor-core M2L waits for 16
                                  bytes more than it copies, so its bounded
@@ -135,6 +150,11 @@ typedef struct {
                               (all 0 without reaction near-field pairs); the
                               box to train the surrogate on                  */
   double reac_near_z_min, reac_near_z_max;
+  double ms_tables;        /* FMM_TABLES: device time of the table build at
+                              create (CUDA events)                           */
+  double table_bytes;      /* FMM_TABLES: device memory of the tables        */
+  long   n_reac_table_classes; /* reaction M2L radial operators of the last
+                              evaluation interpolated from the tables        */
 } fmm_stats_t;
 
 /*
@@ -344,6 +364,24 @@ int fmm_layered_measure_fp64_peak(double* gflops);
 
 /* Statistics of the last create/evaluation. */
 int fmm_layered_stats(const fmm_layered_t* h, fmm_stats_t* stats);
+
+/*
+ * One radial reaction M2L operator interpolated from the tables of a handle
+ * created with FMM_TABLES (Sec. 3.5, eq. metoletableform: the entries
+ * I_{nm,n'm'} as sums of the tabulated S integrals, with the phases and
+ * signs of eq. me2lesimplified; the azimuthal factor e^{i(m'-m)phi} is not
+ * included).  The class is the reaction component (l, l', a, b) (a, b: 0 up,
+ * 1 down) at box width w, target box centre (jt + 1/2) w and image box centre
+ * (js + 1/2) w from the interface (jt, js in {0, 1}) and horizontal distance
+ * w sqrt(R2[r]), R2 = {0, 1, 2, 4, 5, 8, 9, 10, 13, 18}, r in 0..9.
+ *   out  host, [(p+1)^2][(p+1)^2] complex128 interleaved, row (n, m) =
+ *        output coefficient, column (n', m') = input coefficient, flat index
+ *        n^2 + n + m (caller-owned)
+ * Synchronous on the default stream.  FMM_ERR_ARG without tables, for an
+ * absent component or a width outside the tables.
+ */
+int fmm_layered_table_operator(fmm_layered_t* h, int l, int lp, int a, int b, double w, int jt, int js, int r,
+                               double* out);
 
 /*
  * Export of the trees and interaction lists of the last evaluation, for

@@ -21,6 +21,7 @@ FMM_NORM_PAPER = 1
 FMM_MIXED = 2
 FMM_SURROGATE = 4
 FMM_TREE_COUNTS = 8
+FMM_TABLES = 16
 SURR_CELLS = 512          # cells of the surrogate's held-out check (8 x 8 x 8)
 FMM_TEST_STALL_TC = 1 << 30
 
@@ -51,7 +52,9 @@ class Stats(ctypes.Structure):
                 ("gpu_ms_m2l_gemm", ctypes.c_double), ("m2l_gemm_flops", ctypes.c_double),
                 ("m2l_tensor_flops", ctypes.c_double), ("m2l_tc_bytes", ctypes.c_double),
                 ("n_reac_surr_pairs", ctypes.c_long), ("reac_near_rho_max", ctypes.c_double),
-                ("reac_near_z_min", ctypes.c_double), ("reac_near_z_max", ctypes.c_double)]
+                ("reac_near_z_min", ctypes.c_double), ("reac_near_z_max", ctypes.c_double),
+                ("ms_tables", ctypes.c_double), ("table_bytes", ctypes.c_double),
+                ("n_reac_table_classes", ctypes.c_long)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
@@ -60,7 +63,7 @@ EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error
             "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched",
             "fmm_layered_surrogate_train", "fmm_layered_surrogate_report", "fmm_layered_surrogate_set_bound",
             "fmm_layered_surrogate_grad", "fmm_layered_set_components", "fmm_layered_component_work",
-            "fmm_layered_add_components"]
+            "fmm_layered_add_components", "fmm_layered_table_operator"]
 
 _lib = None
 
@@ -112,6 +115,8 @@ def lib():
     L.fmm_layered_tree_export.restype = i
     L.fmm_layered_measure_fp64_peak.argtypes = [d]
     L.fmm_layered_measure_fp64_peak.restype = i
+    L.fmm_layered_table_operator.argtypes = [v, i, i, i, i, ctypes.c_double, i, i, i, d]
+    L.fmm_layered_table_operator.restype = i
     _lib = L
     return L
 
@@ -164,10 +169,12 @@ class LayeredFMM:
     mixed=True runs the M2L translations on the tensor cores (FP16 hi/lo
     operands, FP32 accumulation); every other stage stays FP64.
     tree_counts=True refines reaction trees by the point counts alone
-    (FMM_TREE_COUNTS), so reaction components get near-field pairs."""
+    (FMM_TREE_COUNTS), so reaction components get near-field pairs.
+    tables=True tabulates the reaction M2L integrals at create (FMM_TABLES)
+    and interpolates the reaction operators of every geometry from them."""
 
     def __init__(self, k, d=(), eps=None, p=8, leaf=64, paper_norm=False, mixed=False, surrogate=False,
-                 tree_counts=False, extra_flags=0):
+                 tree_counts=False, tables=False, extra_flags=0):
         L = lib()
         self.k = np.ascontiguousarray(k, dtype=np.float64)
         self.d = np.ascontiguousarray(d, dtype=np.float64)
@@ -178,7 +185,7 @@ class LayeredFMM:
                                   _ptr(self.eps), self.p, self.leaf,
                                   (FMM_NORM_PAPER if paper_norm else FMM_PLAIN_FP64) | (FMM_MIXED if mixed else 0)
                                   | (FMM_SURROGATE if surrogate else 0) | (FMM_TREE_COUNTS if tree_counts else 0)
-                                  | int(extra_flags),
+                                  | (FMM_TABLES if tables else 0) | int(extra_flags),
                                   ctypes.byref(h))
         if rc != 0:
             raise FmmError(rc, L.fmm_layered_last_error(None).decode())
@@ -288,6 +295,16 @@ class LayeredFMM:
             stream = torch.cuda.current_stream(out.device)
         self._check(lib().fmm_layered_add_components(self.h, _ptr(torch.view_as_real(out)),
                                                      ctypes.c_void_p(stream.cuda_stream)))
+        return out
+
+    def table_operator(self, l, lp, a, b, w, jt, js, r):
+        """Radial reaction M2L operator of one class interpolated from the
+        tables (fmm_layered_table_operator): complex [(p+1)^2][(p+1)^2], rows
+        the output coefficients (n, m), columns the input ones."""
+        P = (self.p + 1) ** 2
+        out = np.zeros((P, P), dtype=np.complex128)
+        self._check(lib().fmm_layered_table_operator(self.h, int(l), int(lp), int(a), int(b), float(w), int(jt),
+                                                     int(js), int(r), _ptr(out.view(np.float64))))
         return out
 
     def stats(self):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfmmlayered.so")
-SOURCES = ["medium.cu", "tree.cu", "ops.cu", "p2p.cu", "api.cu", "noalloc.cu", "m2l_gemm.cu", "m2l_tc.cu", "m2l_rot.cu", "surrogate.cu", "sort.cu"]
+SOURCES = ["medium.cu", "tree.cu", "ops.cu", "p2p.cu", "api.cu", "noalloc.cu", "m2l_gemm.cu", "m2l_tc.cu", "m2l_rot.cu", "surrogate.cu", "sort.cu", "tables.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]

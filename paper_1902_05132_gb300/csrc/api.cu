@@ -110,6 +110,11 @@ static void create_impl(fmm_layered* h) {
   FMM_CHECK(cudaStreamSynchronize(0));
   tmpx.release();
   tmpw.release();
+  if (h->flags & FMM_TABLES) {
+    tables_build(h, 0);
+    h->stats.ms_tables = h->tabs.build_ms;
+    h->stats.table_bytes = (double)h->tabs.bytes;
+  }
 }
 
 extern "C" int fmm_layered_create(int n_layers, const double* k, const double* interfaces, const double* eps,
@@ -161,6 +166,7 @@ extern "C" int fmm_layered_create(int n_layers, const double* k, const double* i
 extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   if (!h) return;
   h->surr.release();
+  h->tabs.release();
   if (h->bstream) cudaStreamDestroy(h->bstream);
   if (h->bdone) cudaEventDestroy(h->bdone);
   DevBuf* all[] = {&h->d_k, &h->d_d, &h->d_eps, &h->rule.kr, &h->rule.w, &h->rule.kz, &h->rule.sigma,
@@ -195,6 +201,23 @@ extern "C" const char* fmm_layered_last_error(const fmm_layered_t* h) {
 extern "C" int fmm_layered_stats(const fmm_layered_t* h, fmm_stats_t* s) {
   if (!h || !s) return FMM_ERR_ARG;
   *s = h->stats;
+  return FMM_OK;
+}
+
+extern "C" int fmm_layered_table_operator(fmm_layered_t* h, int l, int lp, int a, int b, double w, int jt, int js,
+                                          int r, double* out) {
+  if (!h || !out) return FMM_ERR_ARG;
+  if (l < 0 || lp < 0 || l >= h->L1 || lp >= h->L1 || a < 0 || a > 1 || b < 0 || b > 1 || !(w > 0)) {
+    h->err = "invalid class";
+    return FMM_ERR_ARG;
+  }
+  try {
+    FMM_CHECK(cudaSetDevice(h->dev));
+    tables_operator_host(h, TabClass{l, lp, a, b, jt, js, r, w, 0}, out, 0);
+  } catch (FmmError& e) {
+    h->err = e.msg;
+    return e.code;
+  }
   return FMM_OK;
 }
 
@@ -434,6 +457,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   // reaction radial operators: only classes present, computed once per geometry
   struct Pending { int c, l, jt, js; std::vector<int> rs; std::vector<long> offs; };
   std::vector<Pending> pend;
+  std::vector<TabClass> tab_cls;
   double tmax = h->rule.ta;
   for (int c = 0; c < nc; ++c) {
     if (comps[c].kind != CK_REAC) continue;
@@ -441,6 +465,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
       double w = cg[c].h2 / (double)(1 << l);
       for (int g = 0; g < 4; ++g) {
         Pending pd{c, l, g / 2, g % 2, {}, {}};
+        const bool by_table = tables_cover(h, w);
         for (int r = 0; r < 10; ++r) {
           if (!used[((size_t)c * 23 + l) * 40 + g * 10 + r]) continue;
           const Comp& C_ = comps[c];
@@ -448,6 +473,13 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
           auto it = oc.rad.find(key);
           if (it != oc.rad.end()) {
             reac_off[((size_t)c * 23 + l) * 40 + g * 10 + r] = it->second;
+          } else if (by_table) {
+            // interpolated from the tabulated integrals (FMM_TABLES)
+            const long npp = (long)(p + 1) * (p + 2) / 2, nmm = (long)p * (p + 1) / 2;
+            long off = cache_alloc(oc.rad_buf, oc.rad_used, npp * npp + nmm * nmm, st);
+            oc.rad[key] = off;
+            reac_off[((size_t)c * 23 + l) * 40 + g * 10 + r] = off;
+            tab_cls.push_back(TabClass{C_.l, C_.lp, C_.a, C_.b, pd.jt, pd.js, r, w, off});
           } else {
             pd.rs.push_back(r);
           }
@@ -523,6 +555,11 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     n_classes += (long)rho.size();
     t_nodes += (long)g.Q * (long)rho.size();
   }
+  if (!tab_cls.empty()) {
+    tables_ops(h, tab_cls, oc.rad_buf.as<cplx>(), st);
+    n_classes += (long)tab_cls.size();
+  }
+  h->stats.n_reac_table_classes = (long)tab_cls.size();
   // any still-missing offsets (classes computed by an earlier evaluation)
   for (int c = 0; c < nc; ++c) {
     if (comps[c].kind != CK_REAC) continue;

@@ -207,6 +207,23 @@ struct SurrState {
   }
 };
 
+// Tabulated reaction M2L integrals (FMM_TABLES; tables.cu): the S integrals
+// of every reaction component on the class rays, the CSR sums that turn them
+// into operator entries, and per-evaluation job buffers.
+struct TabState {
+  bool built = false;
+  int ntab = 0, nslot = 0;
+  double kmax = 0, build_ms = 0;
+  size_t bytes = 0;
+  std::vector<int> slot_of;             // [(l * L1 + l') * 4 + a * 2 + b] -> slot, -1 if none
+  std::vector<long> term_base;          // [(l * L1 + l') * 2 + a] -> offset into term_off, -1 if none
+  DevBuf idx, vals, term_off, term_tab, term_coef, jobs, full, split_offs;
+  void release() {
+    DevBuf* all[] = {&idx, &vals, &term_off, &term_tab, &term_coef, &jobs, &full, &split_offs};
+    for (DevBuf* b : all) b->release();
+  }
+};
+
 struct fmm_layered {
   int L1 = 0;               // number of layers
   std::vector<double> k, d, eps;
@@ -221,6 +238,7 @@ struct fmm_layered {
   TcCache tc;
   RotCache rot;
   SurrState surr;
+  TabState tabs;
   fmm_stats_t stats{};
   std::string err;
   // components evaluated: [comp_first, comp_first + comp_count) of the full
@@ -296,3 +314,10 @@ struct DirectMedium { int L1; double k[FMM_MAXL], d[FMM_MAXL]; };
 void gauss_legendre_pub(int n, std::vector<double>& x, std::vector<double>& w);
 void rule_init(fmm_layered* h);
 void rule_extend(fmm_layered* h, double tmax, cudaStream_t st);
+
+// tables.cu: tabulated reaction M2L integrals (FMM_TABLES)
+struct TabClass { int l, lp, a, b, jt, js, r; double w; long split_off; };
+void tables_build(fmm_layered* h, cudaStream_t st);
+bool tables_cover(const fmm_layered* h, double w);
+void tables_ops(fmm_layered* h, const std::vector<TabClass>& cls, cplx* rad, cudaStream_t st);
+void tables_operator_host(fmm_layered* h, const TabClass& c, double* out, cudaStream_t st);

@@ -189,6 +189,15 @@ static void upload_nodes(fmm_layered* h, const std::vector<cplx>& kr, const std:
   FMM_CHECK(cudaGetLastError());
 }
 
+// sigma and k_z at arbitrary contour nodes (kz [L1][Q], sigma [L1][L1][2][2][Q])
+void launch_sigma_at(fmm_layered* h, int Q, const cplx* kr, cplx* kz, cplx* sigma, cudaStream_t st) {
+  if (Q <= 0) return;
+  dim3 grid((Q + 127) / 128, h->L1);
+  LAUNCH(k_sigma<<<grid, 128, 0, st>>>(h->L1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(), Q, 0,
+                                       kr, kz, sigma));
+  FMM_CHECK(cudaGetLastError());
+}
+
 static void build_nodes(fmm_layered* h, int n_panels, std::vector<cplx>& kr, std::vector<cplx>& w) {
   Rule& R = h->rule;
   std::vector<double> x12, w12, xt, wt;

@@ -387,6 +387,30 @@ __global__ void k_reac_split(int p, const cplx* __restrict__ full, cplx* __restr
   out[e] = acc;
 }
 
+// The same split for a batch of radial operators: operator y of the batch is
+// read at full + y * stride and written at out + offs[y].
+__global__ void k_reac_split_batch(int p, const cplx* __restrict__ full, long stride, const long* __restrict__ offs,
+                                   cplx* __restrict__ out) {
+  const int y = blockIdx.y;
+  const int P = (p + 1) * (p + 1);
+  const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;
+  long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long total = (long)np * np + (long)nm * nm;
+  if (e >= total) return;
+  const cplx* F = full + (long)y * stride;
+  bool plus = e < (long)np * np;
+  int nb = plus ? np : nm;
+  long le = plus ? e : e - (long)np * np;
+  int b = le / nb, a = le % nb;
+  int ia[2], ib[2];
+  double va[2], vb[2];
+  int na = basis_terms(p, a, plus, ia, va), nbt = basis_terms(p, b, plus, ib, vb);
+  cplx acc = C(0, 0);
+  for (int x = 0; x < na; ++x)
+    for (int z = 0; z < nbt; ++z) acc = cadd(acc, cscale(F[(long)ib[z] * P + ia[x]], va[x] * vb[z]));
+  out[offs[y] + e] = acc;
+}
+
 // ---------------------------------------------------------------- P2M
 
 
@@ -694,6 +718,13 @@ void launch_reac_split(int p, const cplx* full, cplx* out, cudaStream_t st) {
   long np = (long)(p + 1) * (p + 2) / 2, nm = (long)p * (p + 1) / 2;
   long total = np * np + nm * nm;
   LAUNCH(k_reac_split<<<(total + 255) / 256, 256, 0, st>>>(p, full, out));
+}
+
+void launch_reac_split_batch(int p, const cplx* full, long stride, const long* offs, int n, cplx* out,
+                             cudaStream_t st) {
+  long np = (long)(p + 1) * (p + 2) / 2, nm = (long)p * (p + 1) / 2;
+  long total = np * np + nm * nm;
+  if (n) LAUNCH(k_reac_split_batch<<<dim3((unsigned)((total + 255) / 256), n), 256, 0, st>>>(p, full, stride, offs, out));
 }
 
 void launch_mark_reac(int nb, BoxGeom B, const CompGeom* cgs, const int* voff, const int* vidx, unsigned char* used,
