@@ -204,7 +204,7 @@ def barycentric(values, x):
     if np.any(d == 0.0):
         return values[int(np.argmin(np.abs(d)))]
     c = lam / d
-    return (c[:, None] * values).sum(axis=0) / c.sum()
+    return (c.reshape((-1,) + (1,) * (values.ndim - 1)) * values).sum(axis=0) / c.sum()
 
 
 def table_T(medium, comp, p, w, jt, js, r, ex=None, nodes=None):
@@ -241,3 +241,79 @@ def degree_weights(medium, comp, p, w):
     st = np.array([(medium.k[l] * rb) ** n / dfact(n) for n in ns])
     ss = np.array([(medium.k[lp] * rb) ** n / dfact(n) for n in ns])
     return st[:, None] * ss[None, :]
+
+
+# ------------------------------------------------ near-field kernel table
+# The reaction near field (Algorithm 1, last step; eq. generalcomponentsimag)
+# needs the kernel u~^{ab}_{ll'} = (i/4pi) S_{0,0,0,0}(rho, zt, zs) at arbitrary
+# target-image pairs.  Its table is a true 3-D one, in the coordinates
+#   u = log2(k_max R), R = sqrt(rho^2 + H^2), H = zt + zs,
+#   theta = atan(rho / H) in [0, atan 6],   f = zt / H in [0, 1],
+# holding R * u~ (which tends to a constant as R -> 0) at 10 x 16 x 8
+# Chebyshev points of the first kind per panel: whole octaves of u from -7
+# to 1, half octaves from 1 to 3.  Pairs outside (R out of range or
+# rho > 6 H) are not tabulated.
+NF_EDGES = tuple([-7.0 + i for i in range(9)] + [1.5, 2.0, 2.5, 3.0])
+NF_NODES = (10, 16, 8)
+NF_THETA_MAX = math.atan(6.0)
+
+
+def near_coords(medium, rho, zt, zs):
+    kmax = float(np.max(medium.k))
+    H = zt + zs
+    R = math.hypot(rho, H)
+    return math.log2(kmax * R), math.atan2(rho, H), zt / H, R
+
+
+def near_panel(u, theta):
+    if not (NF_EDGES[0] <= u <= NF_EDGES[-1]) or theta > NF_THETA_MAX:
+        return None
+    for k in range(len(NF_EDGES) - 1):
+        if u < NF_EDGES[k + 1]:
+            return k
+    return len(NF_EDGES) - 2
+
+
+def near_panel_nodes(medium, comp, k):
+    """R * u~ at the panel's nodes, shape NF_NODES (u, theta, f), by the
+    oracle's quadrature of the kernel (green.reaction_image_kernel)."""
+    from .green import oracle_rule, reaction_image_kernel
+    l, lp, a, b = comp
+    d = medium.d[l] if a == UP else medium.d[l - 1]
+    kmax = float(np.max(medium.k))
+    nu, nt, nf = NF_NODES
+    us = NF_EDGES[k] + 0.5 * (NF_EDGES[k + 1] - NF_EDGES[k]) * (cheb_points(nu) + 1.0)
+    ts = 0.5 * NF_THETA_MAX * (cheb_points(nt) + 1.0)
+    fs = 0.5 * (cheb_points(nf) + 1.0)
+    out = np.zeros(NF_NODES, dtype=complex)
+    for i, uu in enumerate(us):
+        R = 2.0 ** uu / kmax
+        for j, th in enumerate(ts):
+            H, rho = R * math.cos(th), R * math.sin(th)
+            rule = oracle_rule(medium, H, max(rho, 1e-3))
+            for m, f in enumerate(fs):
+                zt, zs = f * H, (1.0 - f) * H
+                zt_abs = d + zt if a == UP else d - zt
+                zs_abs = d - zs if a == UP else d + zs
+                v = reaction_image_kernel(medium, l, lp, a, b, np.array([0.0, 0.0, zt_abs]),
+                                          np.array([[rho, 0.0, zs_abs]]), rule)
+                out[i, j, m] = R * v[0]
+    return out
+
+
+def near_table_value(medium, comp, rho, zt, zs, nodes=None):
+    """Interpolated near-field reaction kernel u~ of one pair; None outside
+    the table.  ``nodes`` may pass near_panel_nodes of the pair's panel."""
+    u, th, f, R = near_coords(medium, rho, zt, zs)
+    k = near_panel(u, th)
+    if k is None:
+        return None
+    if nodes is None:
+        nodes = near_panel_nodes(medium, comp, k)
+    xu = 2.0 * (u - NF_EDGES[k]) / (NF_EDGES[k + 1] - NF_EDGES[k]) - 1.0
+    xt = 2.0 * th / NF_THETA_MAX - 1.0
+    xf = 2.0 * f - 1.0
+    v = barycentric(nodes, xu)                 # (nt, nf)
+    v = barycentric(v, xt)                     # (nf,)
+    v = barycentric(v, xf)
+    return v / R

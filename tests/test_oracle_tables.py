@@ -15,7 +15,10 @@ What pins it, independently of the code under test:
     inside panels of each width (whole, half, quarter octave), with errors
     weighted by the size of the expansion coefficients they multiply;
   * the barycentric formula reproduces the node values and any polynomial of
-    degree < 12 exactly.
+    degree < 12 exactly;
+  * the near-field kernel table (R u~ on Chebyshev points in log2(k_max R),
+    atan(rho/H), zt/H) against the quadrature kernel of eq.
+    generalcomponentsimag at random pairs.
 """
 import math
 
@@ -124,3 +127,36 @@ def test_barycentric_exact_for_low_degree_polynomials():
         want = np.polynomial.polynomial.polyval(x, c)
         assert np.allclose(tb.barycentric(vals, x), want, rtol=1e-12, atol=1e-12)
     assert np.array_equal(tb.barycentric(vals, xn[4]), vals[4])
+
+
+# ---- near-field kernel table (oracle/tables.py, near_*): the interpolated
+# kernel against the quadrature kernel of eq. generalcomponentsimag at random
+# pairs inside a whole-octave and a half-octave panel, and outside the table.
+@pytest.mark.parametrize("comp,k", [((0, 1, UP, DOWN), 5), ((1, 1, DOWN, UP), 10), ((2, 2, DOWN, DOWN), 3)])
+def test_near_table_matches_quadrature_kernel(comp, k):
+    from oracle import green as G
+    l, lp, a, b = comp
+    d = MED.d[l] if a == UP else MED.d[l - 1]
+    nodes = tb.near_panel_nodes(MED, comp, k)
+    rng = np.random.default_rng(11 + k)
+    kmax = max(MED.k)
+    for _ in range(3):
+        u = rng.uniform(tb.NF_EDGES[k], tb.NF_EDGES[k + 1])
+        th = rng.uniform(0.0, tb.NF_THETA_MAX)
+        f = rng.uniform(0.0, 1.0)
+        R = 2.0 ** u / kmax
+        H, rho = R * math.cos(th), R * math.sin(th)
+        zt, zs = f * H, (1.0 - f) * H
+        got = tb.near_table_value(MED, comp, rho, zt, zs, nodes)
+        zt_abs = d + zt if a == UP else d - zt
+        zs_abs = d - zs if a == UP else d + zs
+        rule = G.oracle_rule(MED, H, max(rho, 1e-3))
+        ref = G.reaction_image_kernel(MED, l, lp, a, b, np.array([0.0, 0.0, zt_abs]),
+                                      np.array([[rho, 0.0, zs_abs]]), rule)[0]
+        assert abs(got - ref) <= 1e-9 * abs(ref), (u, th, f, abs(got - ref) / abs(ref))
+
+
+def test_near_table_domain():
+    assert tb.near_table_value(MED, (0, 1, UP, DOWN), 7.0, 0.5, 0.5) is None     # rho > 6 H
+    assert tb.near_panel(3.5, 0.1) is None and tb.near_panel(-7.5, 0.1) is None
+    assert tb.near_panel(-7.0, 0.0) == 0 and tb.near_panel(3.0, 0.0) == len(tb.NF_EDGES) - 2
