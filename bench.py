@@ -303,7 +303,8 @@ def surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, 
     """Count-only reaction trees (FMM_TREE_COUNTS): the reaction components
     get a near field.  FP64 with the quadrature there (the method without
     the network), then the surrogate trained on the (rho, zt, zs) box that
-    near field needs, and the mixed + surrogate form timed on the same trees."""
+    near field needs, and the mixed + surrogate form timed on the same trees;
+    last FP64 with the near-field kernel from the tables (FMM_TABLES)."""
     n = len(w["tgt"])
     out = torch.empty_like(ref_out)
     plain = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True)
@@ -324,6 +325,13 @@ def surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, 
                            nvtx="timed_mixed_surrogate")
     ms_surr.close()
     st_s = sst[-1]
+    # FP64 with the tabulated near-field kernel (FMM_TABLES): no network, no quadrature
+    tab = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True, tables=True)
+    out_t = torch.empty_like(ref_out)
+    tms, tst = timed_evals(torch, tab, src, q, tgt, out_t, args.steps, args.warmup, flush, stream,
+                           nvtx="timed_tables_near")
+    tab.close()
+    st_t = tst[-1]
     res = {
         "trees": "count-only reaction trees (FMM_TREE_COUNTS)",
         "fp64_quadrature": {"value": ws * n / (statistics.mean(qms) * 1e-3), "ms_per_step": statistics.mean(qms),
@@ -339,9 +347,17 @@ def surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, 
                             "surrogate_pairs": st_s["n_reac_surr_pairs"], "reac_pairs": st_s["n_reac_pairs"],
                             "surrogate_fraction": st_s["n_reac_surr_pairs"] / max(1, st_s["n_reac_pairs"]),
                             "rel_l2_vs_fp64_path": _rel(out.cpu().numpy(), ref_out.cpu().numpy())},
+        "fp64_tables": {"value": ws * n / (statistics.mean(tms) * 1e-3), "unit": "particles/s",
+                        "ms_per_step": statistics.mean(tms),
+                        "near_reac_ms": statistics.mean(s["gpu_ms_near_reac"] for s in tst),
+                        "table_pairs": st_t["n_reac_table_pairs"], "reac_pairs": st_t["n_reac_pairs"],
+                        "rel_l2_vs_fp64_quadrature": _rel(out_t.cpu().numpy(), out_q.cpu().numpy()),
+                        "rel_l2_vs_fp64_path": _rel(out_t.cpu().numpy(), ref_out.cpu().numpy())},
     }
     if gold is not None:
         sel = gold["three_layer_sel2000"]
+        res["fp64_tables"]["rel_l2_vs_oracle_direct_2000"] = _rel(out_t.cpu().numpy()[sel],
+                                                                  gold["three_layer_direct2000"])
         res["mixed_surrogate"]["rel_l2_vs_oracle_direct_2000"] = _rel(out.cpu().numpy()[sel],
                                                                       gold["three_layer_direct2000"])
         res["fp64_quadrature"]["rel_l2_vs_oracle_direct_2000"] = _rel(out_q.cpu().numpy()[sel],

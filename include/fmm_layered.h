@@ -90,7 +90,14 @@ extern "C" {
                                  an evaluation interpolates them instead of
                                  integrating, so a new geometry costs no
                                  quadrature.  Classes outside that range use
-                                 the quadrature.  p <= 12 (FMM_ERR_UNSUPPORTED
+                                 the quadrature.  The reaction near field
+                                 takes its kernel from a second table, of
+                                 R u~ on 10 x 16 x 8 Chebyshev points per
+                                 panel in (log2(k_max R), atan(rho/H), zt/H),
+                                 R = |(rho, H)|, H = zt + zs, k_max R in
+                                 [2^-7, 2^3], rho <= 6 H (quadrature outside;
+                                 the surrogate, when trained and attached,
+                                 comes first).  p <= 12 (FMM_ERR_UNSUPPORTED
                                  otherwise); create then takes about a second */
 #define FMM_TEST_STALL_TC (1u << 30) /* test only, with FMM_MIXED: every
                                  stage of the tensor-core M2L waits for 16
@@ -155,6 +162,8 @@ typedef struct {
   double table_bytes;      /* FMM_TABLES: device memory of the tables        */
   long   n_reac_table_classes; /* reaction M2L radial operators of the last
                               evaluation interpolated from the tables        */
+  long   n_reac_table_pairs;   /* FMM_TABLES: of n_reac_pairs, those whose
+                              kernel came from the near-field table          */
 } fmm_stats_t;
 
 /*

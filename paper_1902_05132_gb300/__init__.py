@@ -54,7 +54,7 @@ class Stats(ctypes.Structure):
                 ("n_reac_surr_pairs", ctypes.c_long), ("reac_near_rho_max", ctypes.c_double),
                 ("reac_near_z_min", ctypes.c_double), ("reac_near_z_max", ctypes.c_double),
                 ("ms_tables", ctypes.c_double), ("table_bytes", ctypes.c_double),
-                ("n_reac_table_classes", ctypes.c_long)]
+                ("n_reac_table_classes", ctypes.c_long), ("n_reac_table_pairs", ctypes.c_long)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",

@@ -707,16 +707,18 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   // counters: free pairs, nodes, -, reaction pairs, nodes, surrogate pairs;
   // then the reaction near-field box: max rho, min z, max z (double bits);
   // then the near-field pairs of each component
-  unsigned long long* counters = need<unsigned long long>(ws.iota, 9 + nc);
-  FMM_CHECK(cudaMemsetAsync(counters, 0, 8 * (9 + nc), st));
+  unsigned long long* counters = need<unsigned long long>(ws.iota, 10 + nc);
+  FMM_CHECK(cudaMemsetAsync(counters, 0, 8 * (10 + nc), st));
   FMM_CHECK(cudaMemsetAsync(counters + 7, 0x7F, 8, st));      // min z starts above every finite value
   NB.comp_pairs = counters + 9;
+  NB.tab_pairs = counters + 9 + nc;
   launch_near(dsched + o_near_free, (int)near_free.size(), NB, dnc, make_rule_view(h->rule, coef),
               ws.spos.as<double>(), ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters, err, st,
               (h->flags & FMM_MIXED) != 0);
   E.mark(6, st);
   RuleView rv_reac = make_rule_view(h->rule, coef);
   rv_reac.surr = surrogate_view(h);
+  rv_reac.ntab = near_table_view(h);
   rv_reac.tail_f32 = (h->flags & FMM_MIXED) ? 1 : 0;
   launch_near_reac(dsched + o_near_reac, (int)(reac_items.size() / 2), NB, dnc, rv_reac, ws.spos.as<double>(),
                    ws.sq.as<cplx>(), ws.tpos.as<double>(), phi, counters + 3, counters + 6, st);
@@ -728,10 +730,10 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   FMM_CHECK(cudaGetLastError());
   E.mark(8, st);
   int herr = 0;
-  std::vector<unsigned long long> hcv(9 + nc);
+  std::vector<unsigned long long> hcv(10 + nc);
   unsigned long long* hc = hcv.data();
   FMM_CHECK(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
-  FMM_CHECK(cudaMemcpyAsync(hc, counters, 8 * (9 + nc), cudaMemcpyDeviceToHost, st));
+  FMM_CHECK(cudaMemcpyAsync(hc, counters, 8 * (10 + nc), cudaMemcpyDeviceToHost, st));
   FMM_CHECK(cudaStreamSynchronize(st));
   if (herr & 16) throw FmmError(FMM_ERR_TIMEOUT, "tensor-core M2L: a bounded wait on an mbarrier expired");
   if (herr & 32) throw FmmError(FMM_ERR_TIMEOUT, "near field: a bounded wait for the source copies expired");
@@ -752,6 +754,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.n_reac_pairs = (long)hc[3];
   h->stats.n_reac_nodes = (long)hc[4];
   h->stats.n_reac_surr_pairs = (long)hc[5];
+  h->stats.n_reac_table_pairs = (long)hc[9 + nc];
   {
     double bx[3];
     memcpy(bx, hc + 6, sizeof(bx));

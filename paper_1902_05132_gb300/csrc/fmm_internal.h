@@ -10,6 +10,7 @@
 
 #include "fmm_math.cuh"
 #include "surrogate.cuh"
+#include "near_table.cuh"
 #include "../../include/fmm_layered.h"
 
 #define FMM_CHECK(call)                                                    \
@@ -218,8 +219,11 @@ struct TabState {
   std::vector<int> slot_of;             // [(l * L1 + l') * 4 + a * 2 + b] -> slot, -1 if none
   std::vector<long> term_base;          // [(l * L1 + l') * 2 + a] -> offset into term_off, -1 if none
   DevBuf idx, vals, term_off, term_tab, term_coef, jobs, full, split_offs;
+  // near-field kernel table (near_table.cuh)
+  DevBuf nvals, nslot_map, ncheb;
+  double near_build_ms = 0;
   void release() {
-    DevBuf* all[] = {&idx, &vals, &term_off, &term_tab, &term_coef, &jobs, &full, &split_offs};
+    DevBuf* all[] = {&idx, &vals, &term_off, &term_tab, &term_coef, &jobs, &full, &split_offs, &nvals, &nslot_map, &ncheb};
     for (DevBuf* b : all) b->release();
   }
 };
@@ -299,6 +303,7 @@ struct RuleView {
   int Q, n_near, per_panel, n_panels;
   double ta, panel;
   SurrView surr;           // learned surrogate of the reaction components (w == nullptr: none)
+  NearTabView ntab;        // tabulated near-field reaction kernel (vals == nullptr: none)
   int tail_f32;            // reaction near field: real-axis tail in FP32 (mixed form)
 };
 struct NearComp { int kind, l, lp, a, b; double k; double dref; long coef_off; };
@@ -306,6 +311,7 @@ struct NearBoxes {
   const int *comp, *lev, *sb, *se, *tb, *te, *parent;
   const int *uo, *ui, *wo, *wi, *xo, *xi;
   unsigned long long* comp_pairs;     // near-field pairs per component (added; may be null)
+  unsigned long long* tab_pairs;      // reaction pairs taken from the kernel table (added; may be null)
 };
 struct DirectMedium { int L1; double k[FMM_MAXL], d[FMM_MAXL]; };
 
@@ -321,3 +327,4 @@ void tables_build(fmm_layered* h, cudaStream_t st);
 bool tables_cover(const fmm_layered* h, double w);
 void tables_ops(fmm_layered* h, const std::vector<TabClass>& cls, cplx* rad, cudaStream_t st);
 void tables_operator_host(fmm_layered* h, const TabClass& c, double* out, cudaStream_t st);
+NearTabView near_table_view(const fmm_layered* h);

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ items
   const cplx* coef = R.coef + nc.coef_off;
   const cplx* kzl = R.kz + (long)nc.l * R.Q;
   const cplx* kzp = R.kz + (long)nc.lp * R.Q;
-  unsigned long long my_pairs = 0, my_nodes = 0, my_surr = 0;
+  unsigned long long my_pairs = 0, my_nodes = 0, my_surr = 0, my_tab = 0;
   double rho_hi = 0.0, z_lo = INFINITY, z_hi = 0.0;
   for (int t = t_first + warp; t < t_end; t += 4) {
     const double x = tpos[3 * t], y = tpos[3 * t + 1];
@@ -463,6 +463,15 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ items
               cfma(acc, C((double)v.x * f, (double)v.y * f), qs);
               by_net = true;
               ++my_surr;
+            }
+          }
+          if (!by_net && R.ntab.vals) {
+            // tabulated kernel (FMM_TABLES) where the pair lies inside the table
+            cplx v;
+            if (near_table_eval(R.ntab, slot, rho, zt, zs, &v)) {
+              cfma(acc, v, qs);
+              by_net = true;
+              ++my_tab;
             }
           }
         }
@@ -512,11 +521,13 @@ __global__ void __launch_bounds__(128) k_near_reac(const int* __restrict__ items
     for (int o = 16; o > 0; o >>= 1) {
       my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, o);
       my_surr += __shfl_xor_sync(0xffffffffu, my_surr, o);
+      my_tab += __shfl_xor_sync(0xffffffffu, my_tab, o);
     }
     if (lane == 0 && my_pairs) {
       atomicAdd(&counters[0], my_pairs);
       atomicAdd(&counters[1], my_nodes);
       if (my_surr) atomicAdd(&counters[2], my_surr);
+      if (my_tab && B.tab_pairs) atomicAdd(B.tab_pairs, my_tab);
       if (B.comp_pairs) atomicAdd(&B.comp_pairs[B.comp[T]], my_pairs);
     }
   }
@@ -654,6 +665,7 @@ RuleView make_rule_view(const Rule& R, const cplx* coef) {
   v.ta = R.ta;
   v.panel = R.panel;
   v.surr = SurrView{};
+  v.ntab = NearTabView{};
   v.tail_f32 = 0;
   return v;
 }

@@ -417,6 +417,8 @@ static int tab_slot_index(const fmm_layered* h, int l, int lp, int a, int b) {
   return ((l * h->L1 + lp) * 2 + a) * 2 + b;
 }
 
+static void near_tables_build(fmm_layered* h, const std::vector<int4>& slots, cudaStream_t st);
+
 // Build the tables of every reaction component of the medium (create time).
 void tables_build(fmm_layered* h, cudaStream_t st) {
   TabState& T = h->tabs;
@@ -530,6 +532,9 @@ void tables_build(fmm_layered* h, cudaStream_t st) {
   FMM_CHECK(cudaFuncSetAttribute(k_tab_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LAUNCH(k_tab_build<<<(unsigned)npts, kBuildThreads, smem, st>>>(A));
   FMM_CHECK(cudaGetLastError());
+  T.bytes = sizeof(cplx) * (size_t)npts * T.ntab + sizeof(cplx) * coef_all.size() +
+            sizeof(int) * (tab_all.size() + off_all.size());
+  near_tables_build(h, slots, st);
   FMM_CHECK(cudaEventRecord(e1, st));
   FMM_CHECK(cudaStreamSynchronize(st));      // before the temporaries are freed
   float ms = 0;
@@ -537,8 +542,6 @@ void tables_build(fmm_layered* h, cudaStream_t st) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   T.build_ms = ms;
-  T.bytes = sizeof(cplx) * (size_t)npts * T.ntab + sizeof(cplx) * coef_all.size() +
-            sizeof(int) * (tab_all.size() + off_all.size());
   T.built = true;
 }
 
@@ -616,4 +619,193 @@ void tables_operator_host(fmm_layered* h, const TabClass& c, double* out, cudaSt
       out[2 * ((size_t)i * P + j)] = f[(size_t)j * P + i].x;
       out[2 * ((size_t)i * P + j) + 1] = f[(size_t)j * P + i].y;
     }
+}
+
+// ---------------------------------------------------------------- near-field kernel table
+namespace {
+
+struct NtBuildArgs {
+  const int4* slot;
+  const double* k;
+  double kmax;
+  int L1;
+  int n_near, Qh;
+  const cplx *kr_n, *w_n, *kz_n, *sig_n;
+  int Nt;
+  const int* tail_off;                  // [NT_PANELS + 1]
+  const double *t_t, *w_t;
+  const cplx *kz_t, *sig_t;             // kz [L1][Nt], sigma [L1][L1][2][2][Nt]
+  const double* cheb;                   // NT_CHEB_LEN
+  cplx* vals;
+};
+
+// One CTA per grid line (slot, panel, u point, theta point): the quadrature
+// of u~ at its NT_NF points f, threads splitting the contour nodes, then a
+// block reduction; the table keeps R u~.
+__global__ void __launch_bounds__(128) k_ntab_build(NtBuildArgs A) {
+  int b = blockIdx.x;
+  const int j = b % NT_NTH;
+  b /= NT_NTH;
+  const int i = b % NT_NU;
+  b /= NT_NU;
+  const int panel = b % NT_PANELS;
+  const int slot = b / NT_PANELS;
+  const int4 sl = A.slot[slot];
+  const int l = sl.x, lp = sl.y;
+  const int row = ((l * A.L1 + lp) * 2 + sl.z) * 2 + sl.w;
+  const double* X = A.cheb;
+  const double lo = nt_edge(panel), hi = nt_edge(panel + 1);
+  const double u = lo + 0.5 * (hi - lo) * (X[i] + 1.0);
+  const double R = exp2(u) / A.kmax;
+  const double th = 0.5 * nt_theta_max() * (X[2 * NT_NU + j] + 1.0);
+  const double H = R * cos(th), rho = R * sin(th);
+  double zt[NT_NF], zs[NT_NF];
+#pragma unroll
+  for (int m = 0; m < NT_NF; ++m) {
+    const double f = 0.5 * (X[2 * NT_NU + 2 * NT_NTH + m] + 1.0);
+    zt[m] = f * H;
+    zs[m] = (1.0 - f) * H;
+  }
+  double ar[NT_NF], ai[NT_NF], at[NT_NF];
+#pragma unroll
+  for (int m = 0; m < NT_NF; ++m) ar[m] = ai[m] = at[m] = 0.0;
+  // complex contour: coef = (i/4pi) w k_rho sigma / k_lz
+  for (int q = threadIdx.x; q < A.n_near; q += blockDim.x) {
+    const cplx kr = A.kr_n[q];
+    const cplx kzl = A.kz_n[(long)l * A.Qh + q], kzp = A.kz_n[(long)lp * A.Qh + q];
+    const cplx sg = A.sig_n[(long)row * A.Qh + q];
+    cplx c = cmul(C(0.0, 1.0 / (4.0 * FMM_PI)), cdiv(cmul(cmul(A.w_n[q], kr), sg), kzl));
+    cplx J[1];
+    besselJ_all(0, cscale(kr, rho), J);
+    c = cmul(c, J[0]);
+#pragma unroll
+    for (int m = 0; m < NT_NF; ++m) {
+      const cplx v = cmul(c, cexp_(cadd(cmul(C(0, zt[m]), kzl), cmul(C(0, zs[m]), kzp))));
+      ar[m] += v.x;
+      ai[m] += v.y;
+    }
+  }
+  // real tail: k_jz = i kappa_j, coef = w t sigma / (4 pi kappa_l)
+  for (int q = A.tail_off[panel] + threadIdx.x; q < A.tail_off[panel + 1]; q += blockDim.x) {
+    const double t = A.t_t[q];
+    const double kapl = A.kz_t[(long)l * A.Nt + q].y, kapp = A.kz_t[(long)lp * A.Nt + q].y;
+    const double c = A.w_t[q] * t * A.sig_t[(long)row * A.Nt + q].x / (4.0 * FMM_PI * kapl) * j0(t * rho);
+#pragma unroll
+    for (int m = 0; m < NT_NF; ++m) at[m] += c * exp(-kapl * zt[m] - kapp * zs[m]);
+  }
+  // block reduction: warps by shuffles, then the four warp sums in order
+  __shared__ double red[4][3 * NT_NF];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NT_NF; ++m) {
+    for (int o = 16; o > 0; o >>= 1) {
+      ar[m] += __shfl_xor_sync(0xffffffffu, ar[m], o);
+      ai[m] += __shfl_xor_sync(0xffffffffu, ai[m], o);
+      at[m] += __shfl_xor_sync(0xffffffffu, at[m], o);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < NT_NF; ++m) {
+      red[warp][m] = ar[m];
+      red[warp][NT_NF + m] = ai[m];
+      red[warp][2 * NT_NF + m] = at[m];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NT_NF) {
+    const int m = threadIdx.x;
+    double sr = 0.0, si = 0.0, st = 0.0;
+    for (int w = 0; w < 4; ++w) {
+      sr += red[w][m];
+      si += red[w][NT_NF + m];
+      st += red[w][2 * NT_NF + m];
+    }
+    A.vals[(long)blockIdx.x * NT_NF + m] = C(R * (sr + st), R * si);
+  }
+}
+
+}  // namespace
+
+// Near-field kernel table of every reaction component (create time, with the
+// M2L tables).
+static void near_tables_build(fmm_layered* h, const std::vector<int4>& slots, cudaStream_t st) {
+  TabState& T = h->tabs;
+  const int L1 = h->L1;
+  // Chebyshev points and barycentric weights of the three coordinates
+  std::vector<double> cheb;
+  for (int n : {NT_NU, NT_NTH, NT_NF}) {
+    for (int j = 0; j < n; ++j) cheb.push_back(std::cos((2 * j + 1) * FMM_PI / (2.0 * n)));
+    for (int j = 0; j < n; ++j) cheb.push_back(((j & 1) ? -1.0 : 1.0) * std::sin((2 * j + 1) * FMM_PI / (2.0 * n)));
+  }
+  // real-axis tails per panel: to ta + FMM_NEAR_TAIL_DECAY / H_min, H_min =
+  // R0 cos(theta_max), panels growing from 2 to 6 / R1
+  std::vector<double> xg, wg, tt, tw;
+  gauss_legendre_pub(kTailGL, xg, wg);
+  std::vector<int> tail_off(NT_PANELS + 1, 0);
+  const double ta = h->rule.ta;
+  for (int k = 0; k < NT_PANELS; ++k) {
+    const double R0 = std::exp2(nt_edge(k)) / T.kmax, R1 = std::exp2(nt_edge(k + 1)) / T.kmax;
+    const double tend = ta + FMM_NEAR_TAIL_DECAY / (R0 * std::cos(nt_theta_max()));
+    const double lmax = 6.0 / R1;
+    double len = std::min(2.0, lmax), t = ta;
+    while (t < tend) {
+      for (int i = 0; i < kTailGL; ++i) {
+        tt.push_back(t + 0.5 * len * (xg[i] + 1.0));
+        tw.push_back(0.5 * len * wg[i]);
+      }
+      t += len;
+      len = std::min(1.5 * len, std::max(len, lmax));
+    }
+    tail_off[k + 1] = (int)tt.size();
+  }
+  const int Nt = (int)tt.size();
+  struct Tmp {
+    DevBuf kr, tt, tw, kz, sig, toff, slot;
+    ~Tmp() { kr.release(); tt.release(); tw.release(); kz.release(); sig.release(); toff.release(); slot.release(); }
+  } tmp;
+  std::vector<cplx> krc(Nt);
+  for (int i = 0; i < Nt; ++i) krc[i] = C(tt[i], 0.0);
+  tmp.kr.ensure(sizeof(cplx) * Nt);
+  tmp.tt.ensure(sizeof(double) * Nt);
+  tmp.tw.ensure(sizeof(double) * Nt);
+  tmp.kz.ensure(sizeof(cplx) * (size_t)Nt * L1);
+  tmp.sig.ensure(sizeof(cplx) * (size_t)Nt * L1 * L1 * 4);
+  tmp.toff.ensure(sizeof(int) * tail_off.size());
+  tmp.slot.ensure(sizeof(int4) * slots.size());
+  FMM_CHECK(cudaMemcpyAsync(tmp.kr.ptr, krc.data(), sizeof(cplx) * Nt, cudaMemcpyHostToDevice, st));
+  FMM_CHECK(cudaMemcpyAsync(tmp.tt.ptr, tt.data(), sizeof(double) * Nt, cudaMemcpyHostToDevice, st));
+  FMM_CHECK(cudaMemcpyAsync(tmp.tw.ptr, tw.data(), sizeof(double) * Nt, cudaMemcpyHostToDevice, st));
+  FMM_CHECK(cudaMemcpyAsync(tmp.toff.ptr, tail_off.data(), sizeof(int) * tail_off.size(), cudaMemcpyHostToDevice, st));
+  FMM_CHECK(cudaMemcpyAsync(tmp.slot.ptr, slots.data(), sizeof(int4) * slots.size(), cudaMemcpyHostToDevice, st));
+  launch_sigma_at(h, Nt, tmp.kr.as<cplx>(), tmp.kz.as<cplx>(), tmp.sig.as<cplx>(), st);
+  T.ncheb.ensure(sizeof(double) * cheb.size());
+  FMM_CHECK(cudaMemcpyAsync(T.ncheb.ptr, cheb.data(), sizeof(double) * cheb.size(), cudaMemcpyHostToDevice, st));
+  T.nslot_map.ensure(sizeof(int) * T.slot_of.size());
+  FMM_CHECK(cudaMemcpyAsync(T.nslot_map.ptr, T.slot_of.data(), sizeof(int) * T.slot_of.size(), cudaMemcpyHostToDevice, st));
+  const long lines = (long)slots.size() * NT_PANELS * NT_NU * NT_NTH;
+  T.nvals.ensure(sizeof(cplx) * (size_t)lines * NT_NF);
+  NtBuildArgs A{};
+  A.slot = tmp.slot.as<int4>(); A.k = h->d_k.as<double>(); A.kmax = T.kmax; A.L1 = L1;
+  A.n_near = h->rule.n_near; A.Qh = h->rule.Q();
+  A.kr_n = h->rule.kr.as<cplx>(); A.w_n = h->rule.w.as<cplx>();
+  A.kz_n = h->rule.kz.as<cplx>(); A.sig_n = h->rule.sigma.as<cplx>();
+  A.Nt = Nt; A.tail_off = tmp.toff.as<int>(); A.t_t = tmp.tt.as<double>(); A.w_t = tmp.tw.as<double>();
+  A.kz_t = tmp.kz.as<cplx>(); A.sig_t = tmp.sig.as<cplx>();
+  A.cheb = T.ncheb.as<double>();
+  A.vals = T.nvals.as<cplx>();
+  LAUNCH(k_ntab_build<<<(unsigned)lines, 128, 0, st>>>(A));
+  FMM_CHECK(cudaGetLastError());
+  FMM_CHECK(cudaStreamSynchronize(st));      // before the temporaries are freed
+  T.bytes += sizeof(cplx) * (size_t)lines * NT_NF;
+}
+
+NearTabView near_table_view(const fmm_layered* h) {
+  NearTabView v{};
+  if (!h->tabs.built || !h->tabs.nvals.ptr) return v;
+  v.vals = h->tabs.nvals.as<cplx>();
+  v.slot_of = h->tabs.nslot_map.as<int>();
+  v.cheb = h->tabs.ncheb.as<double>();
+  v.kmax = h->tabs.kmax;
+  return v;
 }

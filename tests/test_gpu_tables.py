@@ -122,3 +122,30 @@ def test_tables_limit_on_order():
     import paper_1902_05132_gb300 as pkg
     with pytest.raises(pkg.FmmError):
         pkg.LayeredFMM(*MED_ARGS, p=13, leaf=64, tables=True)
+
+
+def test_reaction_near_field_from_table_matches_oracle_fmm():
+    # count-only trees: target leaves next to an interface meet image leaves;
+    # their pairs take the kernel from the near-field table
+    from tests.test_gpu_reaction_near import _clustered
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    w = _clustered()
+    src, q, tgt = to_dev(torch, w)
+    st_ = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True, tables=True)
+    got = st_.eval(src, q, tgt).cpu().numpy()
+    st = st_.stats()
+    assert st["n_reac_pairs"] > 0
+    assert st["n_reac_table_pairs"] > 0.9 * st["n_reac_pairs"], (st["n_reac_table_pairs"], st["n_reac_pairs"])
+    sq = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], tree_counts=True)
+    gq = sq.eval(src, q, tgt).cpu().numpy()
+    assert sq.stats()["n_reac_table_pairs"] == 0
+    assert rel_l2(got, gq) < 1e-10, rel_l2(got, gq)
+    sel = workloads.sample_targets(len(w["tgt"]), 150, seed=4)
+    med = Medium(w["k"], w["d"], w["eps"])
+    ref = ofmm.FMM(med, w["p"], w["leaf"], split_interface=False).evaluate(w["src"], w["q"], w["tgt"], targets=sel)
+    err = rel_l2(got[sel], ref)
+    emax = float(np.max(np.abs(got[sel] - ref)) / np.max(np.abs(ref)))
+    assert err < 1e-9 and emax < 1e-9, (err, emax)
+    st_.close()
+    sq.close()
