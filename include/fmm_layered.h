@@ -164,6 +164,16 @@ typedef struct {
                               evaluation interpolated from the tables        */
   long   n_reac_table_pairs;   /* FMM_TABLES: of n_reac_pairs, those whose
                               kernel came from the near-field table          */
+  /* M2L tile autotuner: on the first evaluation with free-space translations
+     (rotation form, p >= 5) the handle times every candidate column tile and
+     block size of that kernel on the evaluation's own translations and keeps
+     the fastest; 0 until then */
+  int    tune_zrot_kc;         /* chosen column tile (translations per CTA)  */
+  int    tune_zrot_threads;    /* chosen threads per CTA                     */
+  int    tune_zrot_candidates; /* candidates timed                           */
+  double tune_zrot_ms;         /* device time of the chosen candidate        */
+  double tune_zrot_rule_ms;    /* ... of the fixed rule (the default tile,
+                                  128 threads), for comparison              */
 } fmm_stats_t;
 
 /*
@@ -370,6 +380,21 @@ int fmm_layered_add_components(fmm_layered_t* h, double* out, void* stream);
  * the FP64 roofline.  Returns FMM_OK and writes *gflops.
  */
 int fmm_layered_measure_fp64_peak(double* gflops);
+
+/*
+ * Let handle h use the device workspace of `owner` (the scratch arrays of an
+ * evaluation: sorted points, trees, lists, expansions, M2L work arrays),
+ * releasing its own if no other handle shares it.  Handles that share a
+ * workspace must not be evaluated at the same time: fmm_layered_eval_batched
+ * runs the problems of such handles one after the other on one stream, so
+ * that a batch of many problems holds as many workspaces as there are
+ * groups instead of one per problem.  Each handle keeps its own operators,
+ * tables and statistics; the tree export and fmm_layered_add_components
+ * describe the last evaluation made in the shared workspace.  Both handles
+ * must belong to the same device (FMM_ERR_ARG otherwise).  Synchronizes the
+ * device.  The paper has no counterpart (it evaluates one problem at a time).
+ */
+int fmm_layered_share_workspace(fmm_layered_t* h, fmm_layered_t* owner);
 
 /* Statistics of the last create/evaluation. */
 int fmm_layered_stats(const fmm_layered_t* h, fmm_stats_t* stats);

@@ -54,7 +54,10 @@ class Stats(ctypes.Structure):
                 ("n_reac_surr_pairs", ctypes.c_long), ("reac_near_rho_max", ctypes.c_double),
                 ("reac_near_z_min", ctypes.c_double), ("reac_near_z_max", ctypes.c_double),
                 ("ms_tables", ctypes.c_double), ("table_bytes", ctypes.c_double),
-                ("n_reac_table_classes", ctypes.c_long), ("n_reac_table_pairs", ctypes.c_long)]
+                ("n_reac_table_classes", ctypes.c_long), ("n_reac_table_pairs", ctypes.c_long),
+                ("tune_zrot_kc", ctypes.c_int), ("tune_zrot_threads", ctypes.c_int),
+                ("tune_zrot_candidates", ctypes.c_int), ("tune_zrot_ms", ctypes.c_double),
+                ("tune_zrot_rule_ms", ctypes.c_double)]
 
 
 EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error", "fmm_layered_eval",
@@ -63,7 +66,7 @@ EXPORTED = ["fmm_layered_create", "fmm_layered_destroy", "fmm_layered_last_error
             "fmm_layered_measure_fp64_peak", "fmm_layered_direct_noalloc", "fmm_layered_eval_batched",
             "fmm_layered_surrogate_train", "fmm_layered_surrogate_report", "fmm_layered_surrogate_set_bound",
             "fmm_layered_surrogate_grad", "fmm_layered_set_components", "fmm_layered_component_work",
-            "fmm_layered_add_components", "fmm_layered_table_operator"]
+            "fmm_layered_add_components", "fmm_layered_table_operator", "fmm_layered_share_workspace"]
 
 _lib = None
 
@@ -117,6 +120,8 @@ def lib():
     L.fmm_layered_measure_fp64_peak.restype = i
     L.fmm_layered_table_operator.argtypes = [v, i, i, i, i, ctypes.c_double, i, i, i, d]
     L.fmm_layered_table_operator.restype = i
+    L.fmm_layered_share_workspace.argtypes = [v, v]
+    L.fmm_layered_share_workspace.restype = i
     _lib = L
     return L
 
@@ -296,6 +301,11 @@ class LayeredFMM:
         self._check(lib().fmm_layered_add_components(self.h, _ptr(torch.view_as_real(out)),
                                                      ctypes.c_void_p(stream.cuda_stream)))
         return out
+
+    def share_workspace(self, owner):
+        """Use the device workspace of another handle (fmm_layered_share_workspace);
+        the two must then not be evaluated at the same time."""
+        self._check(lib().fmm_layered_share_workspace(self.h, owner.h))
 
     def table_operator(self, l, lp, a, b, w, jt, js, r):
         """Radial reaction M2L operator of one class interpolated from the

@@ -163,6 +163,8 @@ extern "C" int fmm_layered_create(int n_layers, const double* k, const double* i
   return FMM_OK;
 }
 
+static void release_workspace(Workspace& ws);
+
 extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   if (!h) return;
   h->surr.release();
@@ -172,7 +174,16 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   DevBuf* all[] = {&h->d_k, &h->d_d, &h->d_eps, &h->rule.kr, &h->rule.w, &h->rule.kz, &h->rule.sigma,
                    &h->tab.gaunt, &h->tab.phase};
   for (DevBuf* b : all) b->release();
-  Workspace& ws = h->ws;
+  if (h->wsp.use_count() == 1) release_workspace(h->W());
+  DevBuf* gb[] = {&h->tc.bbuf, &h->tc.sbuf, &h->tc.phase_f, &h->rot.w, &h->rot.az_buf};
+  for (DevBuf* b : gb) b->release();
+  h->cache.free_buf.release();
+  h->cache.shift_buf.release();
+  h->cache.rad_buf.release();
+  delete h;
+}
+
+static void release_workspace(Workspace& ws) {
   DevBuf* wsb[] = {&ws.slayer, &ws.tlayer, &ws.sorder, &ws.torder, &ws.iota, &ws.ltmp, &ws.counts, &ws.bbox,
                    &ws.gap, &ws.flags, &ws.spos_u, &ws.sq_u, &ws.skey_u, &ws.sval_u, &ws.sidx_u, &ws.tpos_u,
                    &ws.tkey_u, &ws.tval_u, &ws.tidx_u, &ws.skey, &ws.sperm, &ws.spos, &ws.sq, &ws.sidx,
@@ -184,13 +195,21 @@ extern "C" void fmm_layered_destroy(fmm_layered_t* h) {
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
                   &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,
-                  &ws.rot_info, &ws.rot_jobs, &ws.rot_bat, &ws.rot_rs, &ws.rot_tab,
-                  &h->tc.bbuf, &h->tc.sbuf, &h->tc.phase_f, &h->rot.w, &h->rot.az_buf};
+                  &ws.rot_info, &ws.rot_jobs, &ws.rot_bat, &ws.rot_rs, &ws.rot_tab};
   for (DevBuf* b : gb) b->release();
-  h->cache.free_buf.release();
-  h->cache.shift_buf.release();
-  h->cache.rad_buf.release();
-  delete h;
+}
+
+extern "C" int fmm_layered_share_workspace(fmm_layered_t* h, fmm_layered_t* owner) {
+  if (!h || !owner) return FMM_ERR_ARG;
+  if (h->dev != owner->dev) {
+    h->err = "handles on different devices";
+    return FMM_ERR_ARG;
+  }
+  if (h->wsp == owner->wsp) return FMM_OK;
+  cudaDeviceSynchronize();           // no evaluation of h may still use its old workspace
+  if (h->wsp.use_count() == 1) release_workspace(h->W());
+  h->wsp = owner->wsp;
+  return FMM_OK;
 }
 
 extern "C" const char* fmm_layered_last_error(const fmm_layered_t* h) {
@@ -231,7 +250,7 @@ static DirectMedium medium_of(const fmm_layered* h) {
 
 // reaction coefficients for the current rule: [(l,l',a,b)][q]
 static cplx* rule_coef(fmm_layered* h, cudaStream_t st) {
-  cplx* coef = need<cplx>(h->ws.op_tab, (size_t)h->L1 * h->L1 * 4 * h->rule.Q());
+  cplx* coef = need<cplx>(h->W().op_tab, (size_t)h->L1 * h->L1 * 4 * h->rule.Q());
   launch_coef(h->L1, h->rule, coef, st);
   FMM_CHECK(cudaGetLastError());
   return coef;
@@ -304,7 +323,7 @@ static long cache_alloc(DevBuf& buf, long& used, long n_elems, cudaStream_t st) 
 
 static void eval_impl(fmm_layered* h, long ns, const double* src, const double* q, long nt, const double* tgt,
                       double* out, cudaStream_t st) {
-  Workspace& ws = h->ws;
+  Workspace& ws = h->W();
   OpCache& oc = h->cache;
   const int p = h->p, P = (p + 1) * (p + 1);
   const long PP = (long)P * P;
@@ -750,6 +769,11 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   h->stats.gpu_ms_total = E.ms(0, 8);
   h->stats.gpu_ms_m2l_gemm = gemm_ran ? E.ms(10, 11) : 0.0;
   h->stats.m2l_gemm_flops = gemm_flops;
+  h->stats.tune_zrot_kc = h->tune.zrot_kc;
+  h->stats.tune_zrot_threads = h->tune.zrot_threads;
+  h->stats.tune_zrot_ms = h->tune.zrot_ms;
+  h->stats.tune_zrot_rule_ms = h->tune.zrot_rule_ms;
+  h->stats.tune_zrot_candidates = (int)h->tune.zrot_trials.size();
   h->stats.n_free_pairs = (long)hc[0];
   h->stats.n_reac_pairs = (long)hc[3];
   h->stats.n_reac_nodes = (long)hc[4];
@@ -809,9 +833,11 @@ extern "C" int fmm_layered_eval(fmm_layered_t* h, long ns, const double* src, co
 }
 
 // Independent problems, each with its own handle, evaluated concurrently: one
-// host thread per problem (up to 16 at a time) drives that problem's
-// evaluation on the handle's own stream, so that the kernels of different
-// problems overlap on the GPU while each thread waits on its own host steps.
+// host thread per group of problems whose handles share a workspace (up to 16
+// threads at a time; a handle with its own workspace is a group of one)
+// drives those evaluations one after the other on one stream, so that the
+// kernels of different groups overlap on the GPU while each thread waits on
+// its own host steps.
 extern "C" int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const long* ns, const double* const* src,
                                         const double* const* q, const long* nt, const double* const* tgt,
                                         double* const* out, void* stream) {
@@ -835,31 +861,52 @@ extern "C" int fmm_layered_eval_batched(int n, fmm_layered_t* const* hs, const l
     return FMM_ERR_CUDA;
   }
   std::vector<int> rc(n, FMM_OK);
+  // problems whose handles share a workspace form one group, evaluated one
+  // after the other by one thread on the stream of the group's first handle
+  std::vector<std::vector<int>> groups;
+  {
+    std::map<const Workspace*, int> gi;
+    for (int i = 0; i < n; ++i) {
+      auto it = gi.find(hs[i]->wsp.get());
+      if (it == gi.end()) {
+        gi[hs[i]->wsp.get()] = (int)groups.size();
+        groups.push_back({i});
+      } else {
+        groups[it->second].push_back(i);
+      }
+    }
+  }
   std::atomic<int> next{0};
   auto worker = [&]() {
     for (;;) {
-      int i = next.fetch_add(1);
-      if (i >= n) break;
-      fmm_layered* h = hs[i];
-      try {
-        FMM_CHECK(cudaSetDevice(h->dev));
-        if (!h->bstream) FMM_CHECK(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking));
-        if (!h->bdone) FMM_CHECK(cudaEventCreateWithFlags(&h->bdone, cudaEventDisableTiming));
-        FMM_CHECK(cudaStreamWaitEvent(h->bstream, ready, 0));      // inputs written on the caller's stream
-        eval_impl(h, ns[i], src[i], q[i], nt[i], tgt[i], out[i], h->bstream);
-        FMM_CHECK(cudaEventRecord(h->bdone, h->bstream));
-        h->nsrc_last = ns[i];
-        h->ntgt_last = nt[i];
-      } catch (FmmError& e) {
-        h->err = e.msg;
-        rc[i] = e.code;
-      } catch (std::exception& e) {
-        h->err = e.what();
-        rc[i] = FMM_ERR_OOM;
+      int g = next.fetch_add(1);
+      if (g >= (int)groups.size()) break;
+      cudaStream_t gst = nullptr;
+      for (int i : groups[g]) {
+        fmm_layered* h = hs[i];
+        try {
+          FMM_CHECK(cudaSetDevice(h->dev));
+          if (!h->bstream) FMM_CHECK(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking));
+          if (!h->bdone) FMM_CHECK(cudaEventCreateWithFlags(&h->bdone, cudaEventDisableTiming));
+          if (!gst) {
+            gst = h->bstream;
+            FMM_CHECK(cudaStreamWaitEvent(gst, ready, 0));      // inputs written on the caller's stream
+          }
+          eval_impl(h, ns[i], src[i], q[i], nt[i], tgt[i], out[i], gst);
+          FMM_CHECK(cudaEventRecord(h->bdone, gst));
+          h->nsrc_last = ns[i];
+          h->ntgt_last = nt[i];
+        } catch (FmmError& e) {
+          h->err = e.msg;
+          rc[i] = e.code;
+        } catch (std::exception& e) {
+          h->err = e.what();
+          rc[i] = FMM_ERR_OOM;
+        }
       }
     }
   };
-  int nth = std::min(n, 16);
+  int nth = std::min((int)groups.size(), 16);
   std::vector<std::thread> th;
   for (int t = 0; t < nth; ++t) th.emplace_back(worker);
   for (auto& t : th) t.join();
@@ -941,7 +988,7 @@ extern "C" int fmm_layered_add_components(fmm_layered_t* h, double* out, void* s
   try {
     const std::vector<Comp>& comps = h->comps;
     for (size_t c = 0; c < comps.size(); ++c)
-      launch_scatter_add(comps[c].nt, h->ws.tidx.as<int>() + comps[c].to, h->ws.phi.as<cplx>() + comps[c].to, out, st);
+      launch_scatter_add(comps[c].nt, h->W().tidx.as<int>() + comps[c].to, h->W().phi.as<cplx>() + comps[c].to, out, st);
     FMM_CHECK(cudaGetLastError());
   } catch (FmmError& e) {
     h->err = e.msg;
@@ -968,9 +1015,9 @@ extern "C" int fmm_layered_component_info(const fmm_layered_t* hc, int c, long l
   if (!h || c < 0 || c >= (int)h->comps.size() || !info || !root) return FMM_ERR_ARG;
   const Comp& C_ = h->comps[c];
   std::vector<int> comp(h->nboxes);
-  cudaMemcpy(comp.data(), h->ws.bcomp.ptr, 4 * h->nboxes, cudaMemcpyDeviceToHost);
+  cudaMemcpy(comp.data(), h->W().bcomp.ptr, 4 * h->nboxes, cudaMemcpyDeviceToHost);
   std::vector<int> lev(h->nboxes);
-  cudaMemcpy(lev.data(), h->ws.blevel.ptr, 4 * h->nboxes, cudaMemcpyDeviceToHost);
+  cudaMemcpy(lev.data(), h->W().blevel.ptr, 4 * h->nboxes, cudaMemcpyDeviceToHost);
   long nbc = 0;
   int nlev = 0;
   for (int b = 0; b < h->nboxes; ++b)
@@ -1010,14 +1057,14 @@ extern "C" int fmm_layered_tree_export(const fmm_layered_t* hc, int c, int* leve
     if (parent) parent[i] = par[b] < 0 ? -1 : local[par[b]];
   }
   if (src_perm && C_.ns)
-    cudaMemcpy(src_perm, h->ws.slocal.as<int>() + C_.so, 4 * C_.ns, cudaMemcpyDeviceToHost);
+    cudaMemcpy(src_perm, h->W().slocal.as<int>() + C_.so, 4 * C_.ns, cudaMemcpyDeviceToHost);
   if (tgt_perm && C_.nt)
-    cudaMemcpy(tgt_perm, h->ws.tlocal.as<int>() + C_.to, 4 * C_.nt, cudaMemcpyDeviceToHost);
+    cudaMemcpy(tgt_perm, h->W().tlocal.as<int>() + C_.to, 4 * C_.nt, cudaMemcpyDeviceToHost);
   if (list_off) {
     std::vector<int> off(4 * (size_t)(nb + 1));
-    cudaMemcpy(off.data(), h->ws.loff.ptr, 4 * off.size(), cudaMemcpyDeviceToHost);
+    cudaMemcpy(off.data(), h->W().loff.ptr, 4 * off.size(), cudaMemcpyDeviceToHost);
     int* idxs[4] = {v_idx, u_idx, w_idx, x_idx};
-    DevBuf* bufs[4] = {&h->ws.vi, &h->ws.ui, &h->ws.wi, &h->ws.xi};
+    DevBuf* bufs[4] = {&h->W().vi, &h->W().ui, &h->W().wi, &h->W().xi};
     for (int k = 0; k < 4; ++k) {
       const int* o = off.data() + (size_t)k * (nb + 1);
       std::vector<int> all(o[nb]);

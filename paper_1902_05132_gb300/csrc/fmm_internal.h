@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -228,6 +229,15 @@ struct TabState {
   }
 };
 
+// Tile choices of the M2L autotuner (rotation-form kernel k_zrot): made on
+// the first evaluation that has free-space translations, kept per handle.
+struct TuneState {
+  bool zrot_done = false;
+  int zrot_kc = 0, zrot_threads = 0;
+  float zrot_ms = 0, zrot_rule_ms = 0;
+  std::vector<float> zrot_trials;
+};
+
 struct fmm_layered {
   int L1 = 0;               // number of layers
   std::vector<double> k, d, eps;
@@ -237,12 +247,16 @@ struct fmm_layered {
   DevBuf d_k, d_d, d_eps;
   Rule rule;
   Tables tab;
-  Workspace ws;
+  // device workspace of an evaluation; handles may share one
+  // (fmm_layered_share_workspace), which then serializes their evaluations
+  std::shared_ptr<Workspace> wsp = std::make_shared<Workspace>();
+  Workspace& W() const { return *wsp; }
   OpCache cache;
   TcCache tc;
   RotCache rot;
   SurrState surr;
   TabState tabs;
+  TuneState tune;
   fmm_stats_t stats{};
   std::string err;
   // components evaluated: [comp_first, comp_first + comp_count) of the full

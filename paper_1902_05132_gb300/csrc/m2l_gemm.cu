@@ -321,7 +321,7 @@ void run_m2l_gemm(fmm_layered* h, int nb, long nv, const std::vector<std::vector
                   const cplx* l2l_ops, const cplx* M, cplx* L, int* err, cudaStream_t st,
                   cudaEvent_t gemm0, cudaEvent_t gemm1, double* gemm_flops, const std::vector<CompGeom>& cgh,
                   const long* l2l_rot_tab) {
-  Workspace& ws = h->ws;
+  Workspace& ws = h->W();
   const int p = h->p, P = (p + 1) * (p + 1);
   const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;
   if (nv > 0) {

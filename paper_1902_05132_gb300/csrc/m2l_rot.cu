@@ -127,7 +127,7 @@ struct RotBatch {
 };
 
 // Z[col] = W^T A_z conj(W) Y[col] for the columns of one batch (one CTA).
-__global__ void __launch_bounds__(128) k_zrot(int p, int KC, const RotBatch* __restrict__ batches,
+__global__ void __launch_bounds__(256) k_zrot(int p, int KC, const RotBatch* __restrict__ batches,
                                               const cplx* __restrict__ Wall, const cplx* __restrict__ az_ops,
                                               const cplx* __restrict__ Y, cplx* __restrict__ Z) {
   const RotBatch bt = batches[blockIdx.x];
@@ -227,7 +227,7 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
     FMM_CHECK(cudaEventRecord(ev_start, st));
     return;
   }
-  Workspace& ws = h->ws;
+  Workspace& ws = h->W();
   RotCache& R = h->rot;
   const int p = h->p, P = (p + 1) * (p + 1);
   rot_tables(h, st);
@@ -260,22 +260,28 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
     return off;
   };
   const int NW = (int)rot_nw(p), NAZ = rot_naz(p);
-  const int KC = tiling::rot_kc(p);            // column tile (tiling.h)
-  std::vector<RotBatch> bat;
+  std::vector<long> run_az(runs.size());
+  std::vector<int> run_slot(runs.size());
   for (size_t i = 0; i < runs.size(); ++i) {
     const int r = runs[i];
-    const int slot = info[3 * r], comp = info[3 * r + 1], lev = info[3 * r + 2];
-    const long az = az_of(comp, lev, slot);
-    for (int c0 = 0; c0 < cnt[i]; c0 += KC) {
-      RotBatch b{};
-      b.col0 = col0[i] + c0;
-      b.az_off = az;
-      b.K = std::min(KC, cnt[i] - c0);
-      b.slot = slot;
-      bat.push_back(b);
-    }
+    run_slot[i] = info[3 * r];
+    run_az[i] = az_of(info[3 * r + 1], info[3 * r + 2], run_slot[i]);
     *macs += (double)cnt[i] * (2.0 * NW + NAZ);
   }
+  // batches of at most KC columns of one run
+  auto make_batches = [&](int KC, std::vector<RotBatch>& bat) {
+    bat.clear();
+    for (size_t i = 0; i < runs.size(); ++i)
+      for (int c0 = 0; c0 < cnt[i]; c0 += KC) {
+        RotBatch b{};
+        b.col0 = col0[i] + c0;
+        b.az_off = run_az[i];
+        b.K = std::min(KC, cnt[i] - c0);
+        b.slot = run_slot[i];
+        bat.push_back(b);
+      }
+  };
+  std::vector<RotBatch> bat;
   if (!jobs.empty()) {
     R.az_buf.grow_keep(sizeof(cplx) * (size_t)R.az_used, sizeof(cplx) * (size_t)(R.az_used - (long)jobs.size() * P * P),
                        st);
@@ -284,12 +290,51 @@ void run_m2l_rot(fmm_layered* h, const std::vector<int>& runs, const std::vector
     launch_sep_ops(p, dj, (int)jobs.size(), h->tab.gaunt.as<double>(), R.az_buf.as<cplx>(), st);
     FMM_CHECK(cudaGetLastError());
   }
-  RotBatch* db = (RotBatch*)tc_need(ws.rot_bat, sizeof(RotBatch) * bat.size() + 64);
-  FMM_CHECK(cudaMemcpyAsync(db, bat.data(), sizeof(RotBatch) * bat.size(), cudaMemcpyHostToDevice, st));
-  const size_t smem = tiling::rot_smem(p);
-  FMM_CHECK(cudaFuncSetAttribute(k_zrot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // launch with column tile KC and `thr` threads per CTA
+  auto launch = [&](int KC, int thr) {
+    make_batches(KC, bat);
+    RotBatch* db = (RotBatch*)tc_need(ws.rot_bat, sizeof(RotBatch) * bat.size() + 64);
+    FMM_CHECK(cudaMemcpyAsync(db, bat.data(), sizeof(RotBatch) * bat.size(), cudaMemcpyHostToDevice, st));
+    const size_t smem = tiling::rot_smem_kc(p, KC);
+    FMM_CHECK(cudaFuncSetAttribute(k_zrot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return db;
+  };
+  TuneState& T = h->tune;
+  if (!T.zrot_done) {
+    // autotuner: time every candidate tile on this evaluation's own batches
+    // (every candidate computes the same columns, so Z is final either way)
+    // and keep the fastest for the handle; the choice goes to the statistics
+    int kc[16], thr[16];
+    const int nc = tiling::rot_tune_candidates(p, kc, thr, 16);
+    cudaEvent_t a, b;
+    FMM_CHECK(cudaEventCreate(&a));
+    FMM_CHECK(cudaEventCreate(&b));
+    float best = INFINITY;
+    T.zrot_trials.clear();
+    for (int i = 0; i < nc; ++i) {
+      RotBatch* db = launch(kc[i], thr[i]);
+      FMM_CHECK(cudaEventRecord(a, st));
+      const size_t smem = tiling::rot_smem_kc(p, kc[i]);
+      LAUNCH(k_zrot<<<(unsigned)bat.size(), thr[i], smem, st>>>(p, kc[i], db, R.w.as<cplx>(), R.az_buf.as<cplx>(), Y, Z));
+      FMM_CHECK(cudaGetLastError());
+      FMM_CHECK(cudaEventRecord(b, st));
+      FMM_CHECK(cudaEventSynchronize(b));
+      float ms = 0;
+      FMM_CHECK(cudaEventElapsedTime(&ms, a, b));
+      T.zrot_trials.push_back(ms);
+      if (kc[i] == tiling::rot_kc(p) && thr[i] == 128) T.zrot_rule_ms = ms;
+      if (ms < best) { best = ms; T.zrot_kc = kc[i]; T.zrot_threads = thr[i]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    T.zrot_ms = best;
+    T.zrot_done = true;
+  }
+  const int KC = T.zrot_kc, THR = T.zrot_threads;
+  RotBatch* db = launch(KC, THR);
   FMM_CHECK(cudaEventRecord(ev_start, st));   // the translation launches start here
-  LAUNCH(k_zrot<<<(unsigned)bat.size(), 128, smem, st>>>(p, KC, db, R.w.as<cplx>(), R.az_buf.as<cplx>(), Y, Z));
+  LAUNCH(k_zrot<<<(unsigned)bat.size(), THR, tiling::rot_smem_kc(p, KC), st>>>(p, KC, db, R.w.as<cplx>(),
+                                                                             R.az_buf.as<cplx>(), Y, Z));
   FMM_CHECK(cudaGetLastError());
 }
 
@@ -451,7 +496,7 @@ void rot_shift_tables(fmm_layered* h, const std::vector<CompGeom>& cgh, const st
   if (!jobs.empty()) {
     R.az_buf.grow_keep(sizeof(cplx) * (size_t)R.az_used, sizeof(cplx) * (size_t)(R.az_used - (long)jobs.size() * P * P),
                        st);
-    SepJob* dj = (SepJob*)tc_need(h->ws.rot_jobs, sizeof(SepJob) * jobs.size() + 64);
+    SepJob* dj = (SepJob*)tc_need(h->W().rot_jobs, sizeof(SepJob) * jobs.size() + 64);
     FMM_CHECK(cudaMemcpyAsync(dj, jobs.data(), sizeof(SepJob) * jobs.size(), cudaMemcpyHostToDevice, st));
     launch_sep_ops(p, dj, (int)jobs.size(), h->tab.gaunt.as<double>(), R.az_buf.as<cplx>(), st);
     FMM_CHECK(cudaGetLastError());

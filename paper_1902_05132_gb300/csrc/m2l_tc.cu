@@ -536,7 +536,7 @@ void run_m2l_tc(fmm_layered* h, long nv, int nruns, const std::vector<unsigned l
                 OpIndex OI, const std::vector<CompGeom>& cgh, const cplx* free_ops, const cplx* reac_ops,
                 const cplx* M, cplx* Z, int* err, cudaStream_t st, cudaEvent_t gemm0, cudaEvent_t gemm1,
                 double* gemm_flops) {
-  Workspace& ws = h->ws;
+  Workspace& ws = h->W();
   TcCache& tc = h->tc;
   const int p = h->p, P = (p + 1) * (p + 1);
   const int np = (p + 1) * (p + 2) / 2, nm = p * (p + 1) / 2;

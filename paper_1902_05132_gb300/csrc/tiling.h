@@ -81,7 +81,20 @@ inline int rot_kc(int p) {
   if (KC < 8) KC = (int)std::min<size_t>(32, (200 * 1024 - std::min<size_t>(fixed, 200 * 1024)) / col);
   return std::max(KC, 1);
 }
-inline size_t rot_smem(int p) { return rot_fixed_bytes(p) + 2 * kCplx * (size_t)rot_kc(p) * (p + 1) * (p + 1); }
+inline size_t rot_smem_kc(int p, int kc) { return rot_fixed_bytes(p) + 2 * kCplx * (size_t)kc * (p + 1) * (p + 1); }
+inline size_t rot_smem(int p) { return rot_smem_kc(p, rot_kc(p)); }
+// candidates the autotuner of k_zrot times: column tiles that fit one CTA
+// (kc in {4, 8, 16, 24, 32} and the fixed rule's rot_kc) with 128 or 256
+// threads
+inline int rot_tune_candidates(int p, int* kc, int* thr, int max_n) {
+  int kcs[6] = {4, 8, 16, 24, 32, rot_kc(p)};
+  const int nk = (kcs[5] == 4 || kcs[5] == 8 || kcs[5] == 16 || kcs[5] == 24 || kcs[5] == 32) ? 5 : 6;
+  int n = 0;
+  for (int a = 0; a < nk; ++a)
+    for (int t = 128; t <= 256; t += 128)
+      if (rot_smem_kc(p, kcs[a]) <= kSmemPerCta && n < max_n) { kc[n] = kcs[a]; thr[n] = t; ++n; }
+  return n;
+}
 inline size_t shift_smem(int p) { return rot_fixed_bytes(p) + 3 * kCplx * (size_t)(p + 1) * (p + 1); }
 
 }  // namespace tiling

@@ -512,7 +512,7 @@ struct ClassifyOut {
 void tree_host_copy(fmm_layered* h, std::vector<int>& comp, std::vector<int>& lev,
                     std::vector<unsigned long long>& prefix, std::vector<int>& sb, std::vector<int>& se,
                     std::vector<int>& tb, std::vector<int>& te, std::vector<int>& parent) {
-  Workspace& ws = h->ws;
+  Workspace& ws = h->W();
   int nb = h->nboxes;
   comp.resize(nb); lev.resize(nb); prefix.resize(nb); sb.resize(nb); se.resize(nb);
   tb.resize(nb); te.resize(nb); parent.resize(nb);
@@ -530,7 +530,7 @@ void tree_host_copy(fmm_layered* h, std::vector<int>& comp, std::vector<int>& le
 // through `gap_out` ([2][L1][2] minimal distances to interfaces).
 void build_trees(fmm_layered* h, long ns, const double* src, const double* q, long nt, const double* tgt,
                  std::vector<double>& gap_out, cudaStream_t st) {
-  Workspace& ws = h->ws;
+  Workspace& ws = h->W();
   const int L1 = h->L1;
   // ---- classification
   unsigned char* sl = need<unsigned char>(ws.slayer, ns);

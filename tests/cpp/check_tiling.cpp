@@ -48,6 +48,13 @@ int main() {
     // rotation form
     if (rot_kc(p) < 1 || rot_kc(p) > 32) fail("rot column tile", p, rot_kc(p), 32);
     if (rot_smem(p) > kSmemPerCta) fail("rot smem", p, (long)rot_smem(p), (long)kSmemPerCta);
+    {
+      int kc[16], thr[16];
+      int nc = rot_tune_candidates(p, kc, thr, 16);
+      if (nc < 1) fail("rot autotune candidates", p, nc, 1);
+      for (int i = 0; i < nc; ++i)
+        if (rot_smem_kc(p, kc[i]) > kSmemPerCta) fail("rot candidate smem", p, (long)rot_smem_kc(p, kc[i]), (long)kSmemPerCta);
+    }
     if (shift_smem(p) > kSmemPerCta) fail("shift smem", p, (long)shift_smem(p), (long)kSmemPerCta);
     long nw = 0, naz = 0;
     for (int n = 0; n <= p; ++n) nw += (2 * n + 1) * (2 * n + 1);

@@ -34,6 +34,28 @@ def test_batched_equals_separate_evaluations():
             assert np.array_equal(a, b)
 
 
+def test_batched_with_shared_workspaces_equals_separate_evaluations():
+    # ten problems over three workspaces: the problems of a workspace run one
+    # after the other, groups run concurrently; results bit for bit as alone
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    ws, solvers, probs = _problems(torch, 10, seed=5)
+    sep = [s.eval(*pr).cpu().numpy() for s, pr in zip(solvers, probs)]
+    for i in range(3, 10):
+        solvers[i].share_workspace(solvers[i % 3])
+    for _ in range(2):
+        got = [o.cpu().numpy() for o in pkg.eval_batched(solvers, probs)]
+        for a, b in zip(got, sep):
+            assert np.array_equal(a, b)
+    # a handle sharing a workspace still evaluates alone, and closing the
+    # owner first leaves the workspace to the others
+    solvers[0].close()
+    alone = solvers[3].eval(*probs[3]).cpu().numpy()
+    assert np.array_equal(alone, sep[3])
+    for s in solvers[1:]:
+        s.close()
+
+
 def test_batched_many_layers_against_direct_and_oracle():
     torch = cuda_or_skip()
     import paper_1902_05132_gb300 as pkg

@@ -51,3 +51,22 @@ def test_fmm_two_layer_config_all_targets_vs_direct():
     assert rel_l2(dgpu[sel], ref) < 1e-10
     # p = 5: truncation error of the method (Sec. 3.3), not a parity bound
     assert rel_l2(got, dgpu) < 1e-4, rel_l2(got, dgpu)
+
+
+def test_m2l_autotuner_choice_and_identical_results():
+    # the first evaluation times every candidate tile of the rotation-form
+    # M2L (p >= 5) and keeps the fastest; each candidate computes the same
+    # columns, so every later evaluation is bit-identical to the first
+    torch = cuda_or_skip()
+    import paper_1902_05132_gb300 as pkg
+    w = workloads.three_layer(n=4000, leaf=32, p=8)
+    s = pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"])
+    src, q, tgt = to_dev(torch, w)
+    a = s.eval(src, q, tgt).cpu().numpy()
+    st = s.stats()
+    assert st["tune_zrot_candidates"] >= 2
+    assert st["tune_zrot_kc"] >= 1 and st["tune_zrot_threads"] in (128, 256)
+    assert 0 < st["tune_zrot_ms"] <= st["tune_zrot_rule_ms"]
+    b = s.eval(src, q, tgt).cpu().numpy()
+    assert np.array_equal(a, b)
+    s.close()
