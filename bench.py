@@ -21,8 +21,6 @@ Extra keys of the JSON line:
   tables     the reaction M2L from tabulated integrals (FMM_TABLES): table
              build at create, evaluations with a new geometry every step
              with and without the tables, error against the oracle values
-  batched    (only with --batched) 64 independent problems, 2-5 layers,
-             p = 10, mixed form, through fmm_layered_eval_batched
   paper_table  the paper's timing study (Sec. 4, Table 1): irregular domains,
              p = 4, N = 618,256 .. 2,861,288; all components, the 3
              free-space ones and the 3 reaction ones the table selects
@@ -466,66 +464,6 @@ def tables_leg(pkg, torch, w, src, q, tgt, out, args, flush, stream, gold):
     return res
 
 
-def batched_leg(pkg, torch, dev, args, flush, stream, n_problems=64, wave=8):
-    """The batched configuration: 64 independent problems (N log-uniform in
-    [1e4, 2e5], 2-5 layers, p = 10, mixed form) through
-    fmm_layered_eval_batched, in waves of 8 problems (a wave's handles are
-    created, evaluated once cold -- operators built -- and once warm, then
-    destroyed: the 64 problems' translation operators and M2L work arrays
-    do not fit on one GPU at once).  Throughput = all problems' particles
-    over the sum of the waves' times, cold (create + first evaluation, host
-    wall clock) and warm (second evaluation, CUDA events).  Error: four
-    problems of the first wave against the GPU direct sum at 64 sampled
-    targets, and that direct sum against the oracle's at 4 targets."""
-    from paper_1902_05132_gb300 import workloads
-    probs = workloads.batched(n_problems=n_problems)
-    ntot = sum(len(w["tgt"]) for w in probs)
-    cold_s, warm_ms, errs, res = 0.0, 0.0, {}, {}
-    for w0 in range(0, n_problems, wave):
-        grp = probs[w0:w0 + wave]
-        data = [(torch.tensor(w["src"], device=dev), torch.tensor(w["q"], device=dev),
-                 torch.tensor(w["tgt"], device=dev)) for w in grp]
-        outs = [torch.empty(len(w["tgt"]), dtype=torch.complex128, device=dev) for w in grp]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        solvers = [pkg.LayeredFMM(w["k"], w["d"], w["eps"], p=w["p"], leaf=w["leaf"], mixed=True) for w in grp]
-        pkg.eval_batched(solvers, data, outs, stream=stream)
-        torch.cuda.synchronize()
-        cold_s += time.perf_counter() - t0
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pkg.eval_batched(solvers, data, outs, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        warm_ms += e0.elapsed_time(e1)
-        if w0 == 0:
-            for i in (0, 1, 2, 3):
-                w = grp[i]
-                sel = workloads.sample_targets(len(w["tgt"]), 64, seed=i)
-                tsel = data[i][2][torch.tensor(sel, device=dev)]
-                d = solvers[i].direct(data[i][0], data[i][1], tsel).cpu().numpy()
-                errs[w["name"]] = _rel(outs[i].cpu().numpy()[sel], d)
-                if i == 0:
-                    from oracle import green
-                    from oracle.media import Medium
-                    ref = green.direct_sum(Medium(w["k"], w["d"], w["eps"]), w["src"], w["q"], w["tgt"],
-                                           targets=sel[:4])
-                    res["gpu_direct_vs_oracle_direct_4"] = _rel(d[:4], ref)
-        for s_ in solvers:
-            s_.close()
-        del data, outs
-        torch.cuda.empty_cache()
-    res.update({"workload": f"{n_problems} problems, N log-uniform in [1e4, 2e5] (sum {ntot}), 2-5 layers, p = 10, "
-                           f"mixed form, eval_batched in waves of {wave}",
-                "value": ntot / (warm_ms * 1e-3), "unit": "particles/s", "warm_ms": warm_ms,
-                "cold": {"value": ntot / cold_s, "unit": "particles/s", "s": cold_s,
-                         "what": "create + first evaluation (operators built by quadrature) of every wave"},
-                "particles": ntot, "rel_l2_vs_gpu_direct_64": errs})
-    return res
-
-
 def paper_table_leg(pkg, torch, dev, flush, stream):
     """The paper's timing study (Sec. 4, Table 1) on its own workload: the
     irregular domains of workloads.paper_domains scaled to the table's N,
@@ -574,7 +512,6 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-paper-table", action="store_true")
     ap.add_argument("--no-tables", action="store_true")
-    ap.add_argument("--batched", action="store_true", help="also run the 64-problem batched configuration")
     ap.add_argument("--workload", default="three-layer-32768", choices=sorted(WORKLOADS))
     ap.add_argument("--split", default="problems", choices=["problems", "components"])
     args = ap.parse_args()
@@ -754,8 +691,6 @@ def main():
         result["surrogate"] = surrogate_leg(pkg, torch, w, src, q, tgt, ref_out, args, flush, stream, ws, gold)
     if not args.no_large and ws == 1:
         result["large"] = large_leg(pkg, torch, dev, args, flush, stream, _golden())
-    if args.batched and ws == 1:
-        result["batched"] = batched_leg(pkg, torch, dev, args, flush, stream)
     if not args.no_paper_table and ws == 1:
         result["paper_table"] = paper_table_leg(pkg, torch, dev, flush, stream)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:

@@ -16,7 +16,7 @@
 void launch_gaunt(int p, const std::vector<double>& xg, const std::vector<double>& wg, double* G, double* dx,
                   double* dw, cudaStream_t st);
 void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st);
-void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const double* d_rho, const long* d_out_off,
+void launch_reac_group(int p, const ReacGroup& g, const RuleNodes& R, int nr, const double* d_rho, const long* d_out_off,
                        cplx* ops, DevBuf& scratch, cudaStream_t st);
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
                 const cplx* sq, cplx* M, cudaStream_t st);
@@ -191,7 +191,7 @@ static void release_workspace(Workspace& ws) {
                    &ws.bcomp, &ws.blevel, &ws.bprefix, &ws.bsb, &ws.bse, &ws.btb, &ws.bte, &ws.bparent,
                    &ws.bchild0, &ws.bnchild, &ws.bcoord, &ws.lvlcnt, &ws.lvlscan, &ws.lvl_begin, &ws.lcnt,
                    &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
-                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.sort_tmp};
+                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.sort_tmp, &ws.grule};
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
                   &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,
@@ -421,6 +421,9 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
   std::vector<long> m2m_base(nc * 23, -1), l2l_base(nc * 23, -1), m2l_base(nc * 23, -1);
   std::vector<long> reac_off((size_t)nc * 23 * 40, -1);
   std::vector<SepJob> sep_shift, sep_free;
+  // dense free-space M2L operators: read by the tensor-core form and by the
+  // dense FP64 form (p < 5); the FP64 form runs p >= 5 in rotation form
+  const bool dense_free = (h->flags & FMM_MIXED) || p < 5;
   for (int c = 0; c < nc; ++c) {
     for (int l = 2; l <= maxlev; ++l) {
       if (!has_level[c][l]) continue;
@@ -452,7 +455,14 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
         auto key = std::make_pair(dbits(cg[c].kt), dbits(w));
         auto it = oc.free_m2l.find(key);
         long off;
-        if (it == oc.free_m2l.end()) {
+        if (it == oc.free_m2l.end() && !dense_free) {
+          // FP64 path with p >= 5: the free-space translations run in
+          // rotation form (coaxial operators only), so the 343 dense
+          // operators are not built; the offset only names the class
+          off = oc.free_virtual;
+          oc.free_virtual += 343 * PP;
+          oc.free_m2l[key] = off;
+        } else if (it == oc.free_m2l.end()) {
           off = cache_alloc(oc.free_buf, oc.free_used, 343 * PP, st);
           oc.free_m2l[key] = off;
           for (int dz = -3; dz <= 3; ++dz)
@@ -503,11 +513,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
             pd.rs.push_back(r);
           }
         }
-        if (!pd.rs.empty()) {
-          pend.push_back(pd);
-          double H = (pd.jt + pd.js + 1) * w;
-          tmax = std::max(tmax, h->rule.ta + (30.0 + 7.0 * p) / H);
-        }
+        if (!pd.rs.empty()) pend.push_back(pd);     // each group integrates on its own rule (group_rule)
       }
     }
   }
@@ -543,8 +549,11 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     g.kl = h->k[C_.l]; g.klp = h->k[C_.lp];
     g.zt = (pd.jt + 0.5) * w;
     g.zs = (pd.js + 0.5) * w;
-    g.sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * Q;
-    g.Q = h->rule.nodes_to(h->rule.ta + (30.0 + 7.0 * p) / (g.zt + g.zs));
+    double rho_max = 0.0;
+    for (int r : pd.rs) rho_max = std::max(rho_max, sqrt((double)RHO2[r]) * w);
+    const RuleNodes RN = group_rule(h, g.zt + g.zs, rho_max, ws.grule, st);
+    g.sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * RN.Q;
+    g.Q = RN.Q;
     std::vector<double> rho;
     std::vector<long> offs, split_offs;
     const long npp = (long)(p + 1) * (p + 2) / 2, nmm = (long)p * (p + 1) / 2;
@@ -566,7 +575,7 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     memcpy(blob.data(), rho.data(), sizeof(double) * rho.size());
     memcpy(blob.data() + sizeof(double) * 10, offs.data(), sizeof(long) * offs.size());
     FMM_CHECK(cudaMemcpyAsync(drho, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
-    launch_reac_group(p, g, h->rule, (int)rho.size(), drho, doff, full, ws.m2l_reac, st);
+    launch_reac_group(p, g, RN, (int)rho.size(), drho, doff, full, ws.m2l_reac, st);
     for (size_t k = 0; k < rho.size(); ++k)
       launch_reac_split(p, full + offs[k], oc.rad_buf.as<cplx>() + split_offs[k], st);
     FMM_CHECK(cudaGetLastError());

@@ -123,6 +123,14 @@ struct Rule {
   double near_tmax(double H) const { return ta + FMM_NEAR_TAIL_DECAY / H; }
 };
 
+// Contour nodes of one integration (the handle's rule, or a rule built for
+// one group of reaction M2L classes): kr, w [Q]; kz [L1][Q]; sigma
+// [L1][L1][2][2][Q]; nodes [0, n_near) complex, the rest on the real tail.
+struct RuleNodes {
+  const cplx *kr, *w, *kz, *sigma;
+  int Q, n_near;
+};
+
 struct Tables {             // expansion-order dependent tables built at create
   DevBuf gaunt;             // double [P][P][2p+1], G(n,m; nu,-mu; q)
   DevBuf phase;             // cplx [49][2p+1], azimuthal phases of the reaction M2L offsets
@@ -154,6 +162,7 @@ struct Workspace {
   DevBuf rot_info, rot_jobs, rot_bat, rot_rs, rot_tab;
   DevBuf out_tmp;
   DevBuf sort_tmp;
+  DevBuf grule;         // contour nodes of the reaction M2L group being integrated
 };
 
 // Translation operators kept across evaluations: they depend only on the box
@@ -162,11 +171,12 @@ struct Workspace {
 struct OpCache {
   DevBuf free_buf, shift_buf, rad_buf;
   long free_used = 0, shift_used = 0, rad_used = 0;      // elements (cplx)
+  long free_virtual = 0;    // class offsets of free-space operators that are not built (rotation form)
   std::map<std::pair<uint64_t, uint64_t>, long> free_m2l;              // (k, w) -> 343 slots
   std::map<std::tuple<uint64_t, uint64_t, int>, long> shift;           // (k, w, kind) -> 8 octants
   std::map<std::tuple<int, int, int, int, uint64_t, int, int, int>, long> rad;  // (l,l',a,b,w,jt,js,r)
   void clear() {
-    free_used = shift_used = rad_used = 0;
+    free_used = shift_used = rad_used = free_virtual = 0;
     free_m2l.clear();
     shift.clear();
     rad.clear();
@@ -334,6 +344,9 @@ struct DirectMedium { int L1; double k[FMM_MAXL], d[FMM_MAXL]; };
 void gauss_legendre_pub(int n, std::vector<double>& x, std::vector<double>& w);
 void rule_init(fmm_layered* h);
 void rule_extend(fmm_layered* h, double tmax, cudaStream_t st);
+// nodes for the reaction M2L classes of one group: the handle's complex
+// contour, then a real tail to ta + (30 + 7p)/H in panels scaled to the group
+RuleNodes group_rule(fmm_layered* h, double H, double rho_max, DevBuf& buf, cudaStream_t st);
 
 // tables.cu: tabulated reaction M2L integrals (FMM_TABLES)
 struct TabClass { int l, lp, a, b, jt, js, r; double w; long split_off; };

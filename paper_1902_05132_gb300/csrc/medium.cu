@@ -267,3 +267,64 @@ void rule_extend(fmm_layered* h, double tmax, cudaStream_t st) {
   R.kr.release(); R.w.release(); R.kz.release(); R.sigma.release();
   upload_nodes(h, kr, w, 0, st);
 }
+
+// ---------------------------------------------------------------- rules of reaction M2L groups
+// Copy the complex contour nodes of the handle's rule into a group's node
+// block (kr, w, kz, sigma with the group's stride Qg).
+__global__ void k_rule_near_copy(int L1, int n_near, int Qh, const cplx* __restrict__ kr, const cplx* __restrict__ w,
+                                 const cplx* __restrict__ kz, const cplx* __restrict__ sigma, int Qg,
+                                 cplx* __restrict__ gkr, cplx* __restrict__ gw, cplx* __restrict__ gkz,
+                                 cplx* __restrict__ gsig) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_near) return;
+  gkr[q] = kr[q];
+  gw[q] = w[q];
+  for (int j = 0; j < L1; ++j) gkz[(long)j * Qg + q] = kz[(long)j * Qh + q];
+  for (int r = 0; r < L1 * L1 * 4; ++r) gsig[(long)r * Qg + q] = sigma[(long)r * Qh + q];
+}
+
+// Nodes for the reaction M2L classes of one group (vertical centre gap H,
+// largest horizontal offset rho_max): the handle's complex contour up to ta,
+// then the real tail to ta + (30 + 7p)/H -- the end the handle's rule would
+// need -- in Gauss-Legendre panels whose length grows from min(2, Lmax) by
+// 1.5x per panel to Lmax = 4 / max(rho_max, H), i.e. at most 4 radians of the
+// Bessel factor's oscillation and a factor e^4 of the decay per panel.  The
+// node count then stays near 1,500 as H shrinks, where fixed panels of length
+// 2 need 8 (30 + 7p)/H nodes (a faster precompute of the operators, the
+// paper's closing remark on quadrature rules).  sigma and k_z are computed at
+// the tail nodes (k_sigma).  buf holds the nodes until the next call.
+RuleNodes group_rule(fmm_layered* h, double H, double rho_max, DevBuf& buf, cudaStream_t st) {
+  Rule& R = h->rule;
+  const int L1 = h->L1, p = h->p;
+  std::vector<double> xg, wg;
+  gauss_legendre(R.per_panel, xg, wg);
+  std::vector<cplx> kr, w;
+  const double tend = R.ta + (30.0 + 7.0 * p) / H;
+  const double lmax = 4.0 / std::max(rho_max, H);
+  double len = std::min(2.0, lmax), t = R.ta;
+  while (t < tend) {
+    for (int i = 0; i < R.per_panel; ++i) {
+      kr.push_back(C(t + 0.5 * len * (xg[i] + 1.0), 0.0));
+      w.push_back(C(0.5 * len * wg[i], 0.0));
+    }
+    t += len;
+    len = std::min(1.5 * len, std::max(len, lmax));
+  }
+  const int nn = R.n_near, Qg = nn + (int)kr.size();
+  const size_t nodes = (size_t)Qg * (2 + L1 + 4 * L1 * L1);
+  buf.ensure(sizeof(cplx) * nodes);
+  cplx* gkr = buf.as<cplx>();
+  cplx* gw = gkr + Qg;
+  cplx* gkz = gw + Qg;
+  cplx* gsig = gkz + (size_t)L1 * Qg;
+  FMM_CHECK(cudaMemcpyAsync(gkr + nn, kr.data(), sizeof(cplx) * kr.size(), cudaMemcpyHostToDevice, st));
+  FMM_CHECK(cudaMemcpyAsync(gw + nn, w.data(), sizeof(cplx) * w.size(), cudaMemcpyHostToDevice, st));
+  LAUNCH(k_rule_near_copy<<<(nn + 127) / 128, 128, 0, st>>>(L1, nn, R.Q(), R.kr.as<cplx>(), R.w.as<cplx>(),
+                                                             R.kz.as<cplx>(), R.sigma.as<cplx>(), Qg, gkr, gw, gkz,
+                                                             gsig));
+  dim3 grid((unsigned)((Qg - nn + 127) / 128), L1);
+  LAUNCH(k_sigma<<<grid, 128, 0, st>>>(L1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(), Qg, nn,
+                                       gkr, gkz, gsig));
+  FMM_CHECK(cudaGetLastError());
+  return RuleNodes{gkr, gw, gkz, gsig, Qg, nn};
+}

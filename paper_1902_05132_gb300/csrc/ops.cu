@@ -666,8 +666,8 @@ void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx*
 }
 
 // Radial reaction M2L matrices of one group for nr radial classes.
-void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const double* d_rho, const long* d_out_off,
-                       cplx* ops, DevBuf& scratch, cudaStream_t st) {
+void launch_reac_group(int p, const ReacGroup& g, const RuleNodes& R, int nr, const double* d_rho,
+                       const long* d_out_off, cplx* ops, DevBuf& scratch, cudaStream_t st) {
   const int P = (p + 1) * (p + 1);
   const int D = 2 * p + 1;
   const int nn = std::min(R.n_near, g.Q), Qt = g.Q - nn;
@@ -681,10 +681,9 @@ void launch_reac_group(int p, const ReacGroup& g, const Rule& R, int nr, const d
   double* Br = Ar + (size_t)Qt * P;
   cplx* Jc = (cplx*)(Br + (size_t)Qt * P);
   double* Jr = (double*)(Jc + (size_t)nr * nn * D);
-  LAUNCH(k_reac_nodes<<<(g.Q + 127) / 128, 128, 0, st>>>(p, g, nn, R.kr.as<cplx>(), R.w.as<cplx>(), R.kz.as<cplx>(),
-                                                          R.Q(), R.sigma.as<cplx>(), Ac, Bc, Ar, Br));
+  LAUNCH(k_reac_nodes<<<(g.Q + 127) / 128, 128, 0, st>>>(p, g, nn, R.kr, R.w, R.kz, R.Q, R.sigma, Ac, Bc, Ar, Br));
   long ne = (long)g.Q * nr;
-  LAUNCH(k_reac_bessel<<<(ne + 127) / 128, 128, 0, st>>>(p, g.Q, nn, nr, d_rho, R.kr.as<cplx>(), Jc, Jr));
+  LAUNCH(k_reac_bessel<<<(ne + 127) / 128, 128, 0, st>>>(p, g.Q, nn, nr, d_rho, R.kr, Jc, Jr));
   size_t smem = sizeof(double) * (2 * TQR * (FMM_MAXP + 1) + 2 * TQR * P + 2 * TQR * D);
   FMM_CHECK(cudaFuncSetAttribute(k_reac_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int threads = 256;
