@@ -18,6 +18,7 @@ void launch_gaunt(int p, const std::vector<double>& xg, const std::vector<double
 void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx* ops, cudaStream_t st);
 void launch_reac_group(int p, const ReacGroup& g, const RuleNodes& R, int nr, const double* d_rho, const long* d_out_off,
                        cplx* ops, DevBuf& scratch, cudaStream_t st);
+size_t reac_group_scratch(int p, int Q, int n_near, int nr);
 void launch_p2m(int p, const int* leaves, int n, BoxGeom B, const CompGeom* cgs, const double* spos,
                 const cplx* sq, cplx* M, cudaStream_t st);
 void launch_m2m(int p, const int* boxes, int n, BoxGeom B, const long* op_base, const cplx* ops, cplx* M,
@@ -191,7 +192,8 @@ static void release_workspace(Workspace& ws) {
                    &ws.bcomp, &ws.blevel, &ws.bprefix, &ws.bsb, &ws.bse, &ws.btb, &ws.bte, &ws.bparent,
                    &ws.bchild0, &ws.bnchild, &ws.bcoord, &ws.lvlcnt, &ws.lvlscan, &ws.lvl_begin, &ws.lcnt,
                    &ws.loff, &ws.vi, &ws.ui, &ws.wi, &ws.xi, &ws.M, &ws.L, &ws.m2l_free, &ws.m2m_op,
-                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.sort_tmp, &ws.grule};
+                   &ws.l2l_op, &ws.m2l_reac, &ws.op_tab, &ws.phi, &ws.out_tmp, &ws.sort_tmp, &ws.grule,
+                   &ws.gargs};
   for (DevBuf* b : wsb) b->release();
   DevBuf* gb[] = {&ws.g_owner, &ws.g_keys, &ws.g_vals, &ws.g_inv, &ws.g_Y, &ws.g_Z, &ws.g_runs, &ws.g_bat,
                   &ws.tc_runs, &ws.tc_jobs, &ws.tc_a, &ws.tc_sig, &ws.tc_parts, &ws.tc_items, &ws.tc_etab,
@@ -541,47 +543,90 @@ static void eval_impl(fmm_layered* h, long ns, const double* src, const double* 
     launch_sep_ops(p, dj + sep_shift.size(), (int)sep_free.size(), h->tab.gaunt.as<double>(), oc.free_buf.as<cplx>(), st);
     FMM_CHECK(cudaGetLastError());
   }
-  for (Pending& pd : pend) {
-    const Comp& C_ = comps[pd.c];
-    double w = cg[pd.c].h2 / (double)(1 << pd.l);
-    ReacGroup g{};
-    g.l = C_.l; g.lp = C_.lp; g.a = C_.a; g.b = C_.b;
-    g.kl = h->k[C_.l]; g.klp = h->k[C_.lp];
-    g.zt = (pd.jt + 0.5) * w;
-    g.zs = (pd.js + 0.5) * w;
-    double rho_max = 0.0;
-    for (int r : pd.rs) rho_max = std::max(rho_max, sqrt((double)RHO2[r]) * w);
-    const RuleNodes RN = group_rule(h, g.zt + g.zs, rho_max, ws.grule, st);
-    g.sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * RN.Q;
-    g.Q = RN.Q;
+  // reaction groups by quadrature: plan every group on the host (its own
+  // scale-adapted rule, cache slots of its classes), upload the nodes and the
+  // small argument arrays of all groups at once, then launch the groups one
+  // after the other without synchronizing in between
+  struct GroupPlan {
+    ReacGroup g;
     std::vector<double> rho;
-    std::vector<long> offs, split_offs;
+    std::vector<long> split;
+    long node0;              // first node of the group in the concatenated node arrays
+  };
+  std::vector<GroupPlan> plans;
+  std::vector<cplx> hkr, hw;
+  {
     const long npp = (long)(p + 1) * (p + 2) / 2, nmm = (long)p * (p + 1) / 2;
     const long split_elems = npp * npp + nmm * nmm;
-    for (size_t k = 0; k < pd.rs.size(); ++k) {
-      int r = pd.rs[k];
-      rho.push_back(sqrt((double)RHO2[r]) * w);
-      offs.push_back((long)k * PP);                 // full radial matrix in scratch
-      long off = cache_alloc(oc.rad_buf, oc.rad_used, split_elems, st);
-      split_offs.push_back(off);
-      oc.rad[std::make_tuple(C_.l, C_.lp, C_.a, C_.b, dbits(w), pd.jt, pd.js, r)] = off;
-      reac_off[((size_t)pd.c * 23 + pd.l) * 40 + (pd.jt * 2 + pd.js) * 10 + r] = off;
+    const int nn = h->rule.n_near;
+    for (Pending& pd : pend) {
+      const Comp& C_ = comps[pd.c];
+      const double w = cg[pd.c].h2 / (double)(1 << pd.l);
+      GroupPlan gp;
+      ReacGroup& g = gp.g;
+      g = ReacGroup{};
+      g.l = C_.l; g.lp = C_.lp; g.a = C_.a; g.b = C_.b;
+      g.kl = h->k[C_.l]; g.klp = h->k[C_.lp];
+      g.zt = (pd.jt + 0.5) * w;
+      g.zs = (pd.js + 0.5) * w;
+      double rho_max = 0.0;
+      for (int r : pd.rs) rho_max = std::max(rho_max, sqrt((double)RHO2[r]) * w);
+      gp.node0 = (long)hkr.size();
+      hkr.resize(hkr.size() + nn, C(0, 0));          // complex contour: filled on the device
+      hw.resize(hw.size() + nn, C(0, 0));
+      g.Q = nn + group_tail(h, g.zt + g.zs, rho_max, hkr, hw);
+      g.sig_off = ((((long)C_.l * h->L1 + C_.lp) * 2 + C_.a) * 2 + C_.b) * g.Q;
+      for (int r : pd.rs) {
+        gp.rho.push_back(sqrt((double)RHO2[r]) * w);
+        long off = cache_alloc(oc.rad_buf, oc.rad_used, split_elems, st);
+        gp.split.push_back(off);
+        oc.rad[std::make_tuple(C_.l, C_.lp, C_.a, C_.b, dbits(w), pd.jt, pd.js, r)] = off;
+        reac_off[((size_t)pd.c * 23 + pd.l) * 40 + (pd.jt * 2 + pd.js) * 10 + r] = off;
+      }
+      plans.push_back(std::move(gp));
     }
+  }
+  if (!plans.empty()) {
+    const int L1 = h->L1;
+    const long ntot = (long)hkr.size();
+    cplx* nodes = need<cplx>(ws.grule, (size_t)ntot * (2 + L1 + 4 * L1 * L1));
+    cplx* kr_all = nodes;
+    cplx* w_all = kr_all + ntot;
+    cplx* kz_all = w_all + ntot;                       // group g: [L1][Q_g] at L1 * node0
+    cplx* sig_all = kz_all + (size_t)L1 * ntot;        // group g: [L1][L1][2][2][Q_g] at 4 L1^2 * node0
+    FMM_CHECK(cudaMemcpyAsync(kr_all, hkr.data(), sizeof(cplx) * ntot, cudaMemcpyHostToDevice, st));
+    FMM_CHECK(cudaMemcpyAsync(w_all, hw.data(), sizeof(cplx) * ntot, cudaMemcpyHostToDevice, st));
+    // per group: 10 radial distances and 10 output offsets
+    std::vector<char> blob(plans.size() * (sizeof(double) * 10 + sizeof(long) * 10), 0);
+    size_t scratch = 0;
+    for (size_t i = 0; i < plans.size(); ++i) {
+      char* b = blob.data() + i * (sizeof(double) * 10 + sizeof(long) * 10);
+      memcpy(b, plans[i].rho.data(), sizeof(double) * plans[i].rho.size());
+      for (size_t k = 0; k < plans[i].rho.size(); ++k) {
+        long o = (long)k * PP;                          // full radial matrix k of the group in scratch
+        memcpy(b + sizeof(double) * 10 + sizeof(long) * k, &o, sizeof(long));
+      }
+      scratch = std::max(scratch, reac_group_scratch(p, plans[i].g.Q, h->rule.n_near, (int)plans[i].rho.size()));
+    }
+    char* dargs = need<char>(ws.gargs, blob.size());
+    FMM_CHECK(cudaMemcpyAsync(dargs, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
+    ws.m2l_reac.ensure(scratch);                        // sized once: no reallocation between launches
     cplx* full = need<cplx>(ws.out_tmp, (size_t)PP * 10 + 64);
-    // small per-group argument arrays: stream-ordered uploads from a pinned-free host copy
-    double* drho = (double*)(full + (size_t)PP * 10);
-    long* doff = (long*)(drho + 10);
-    std::vector<char> blob(sizeof(double) * 10 + sizeof(long) * 10, 0);
-    memcpy(blob.data(), rho.data(), sizeof(double) * rho.size());
-    memcpy(blob.data() + sizeof(double) * 10, offs.data(), sizeof(long) * offs.size());
-    FMM_CHECK(cudaMemcpyAsync(drho, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
-    launch_reac_group(p, g, RN, (int)rho.size(), drho, doff, full, ws.m2l_reac, st);
-    for (size_t k = 0; k < rho.size(); ++k)
-      launch_reac_split(p, full + offs[k], oc.rad_buf.as<cplx>() + split_offs[k], st);
+    for (size_t i = 0; i < plans.size(); ++i) {
+      const GroupPlan& gp = plans[i];
+      const long n0 = gp.node0;
+      const RuleNodes RN{kr_all + n0, w_all + n0, kz_all + (size_t)L1 * n0, sig_all + (size_t)4 * L1 * L1 * n0,
+                         gp.g.Q, h->rule.n_near};
+      group_rule_fill(h, RN, st);
+      const double* drho = (const double*)(dargs + i * (sizeof(double) * 10 + sizeof(long) * 10));
+      const long* doff = (const long*)(drho + 10);
+      launch_reac_group(p, gp.g, RN, (int)gp.rho.size(), drho, doff, full, ws.m2l_reac, st);
+      for (size_t k = 0; k < gp.rho.size(); ++k)
+        launch_reac_split(p, full + (long)k * PP, oc.rad_buf.as<cplx>() + gp.split[k], st);
+      n_classes += (long)gp.rho.size();
+      t_nodes += (long)gp.g.Q * (long)gp.rho.size();
+    }
     FMM_CHECK(cudaGetLastError());
-    FMM_CHECK(cudaStreamSynchronize(st));     // the argument blob is reused by the next group
-    n_classes += (long)rho.size();
-    t_nodes += (long)g.Q * (long)rho.size();
   }
   if (!tab_cls.empty()) {
     tables_ops(h, tab_cls, oc.rad_buf.as<cplx>(), st);

@@ -162,7 +162,8 @@ struct Workspace {
   DevBuf rot_info, rot_jobs, rot_bat, rot_rs, rot_tab;
   DevBuf out_tmp;
   DevBuf sort_tmp;
-  DevBuf grule;         // contour nodes of the reaction M2L group being integrated
+  DevBuf grule;         // contour nodes of the reaction M2L groups being integrated
+  DevBuf gargs;         // their radial distances and output offsets
 };
 
 // Translation operators kept across evaluations: they depend only on the box
@@ -346,7 +347,8 @@ void rule_init(fmm_layered* h);
 void rule_extend(fmm_layered* h, double tmax, cudaStream_t st);
 // nodes for the reaction M2L classes of one group: the handle's complex
 // contour, then a real tail to ta + (30 + 7p)/H in panels scaled to the group
-RuleNodes group_rule(fmm_layered* h, double H, double rho_max, DevBuf& buf, cudaStream_t st);
+int group_tail(const fmm_layered* h, double H, double rho_max, std::vector<cplx>& kr, std::vector<cplx>& w);
+void group_rule_fill(fmm_layered* h, const RuleNodes& G, cudaStream_t st);
 
 // tables.cu: tabulated reaction M2L integrals (FMM_TABLES)
 struct TabClass { int l, lp, a, b, jt, js, r; double w; long split_off; };

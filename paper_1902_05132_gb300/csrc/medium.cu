@@ -290,41 +290,45 @@ __global__ void k_rule_near_copy(int L1, int n_near, int Qh, const cplx* __restr
 // 1.5x per panel to Lmax = 4 / max(rho_max, H), i.e. at most 4 radians of the
 // Bessel factor's oscillation and a factor e^4 of the decay per panel.  The
 // node count then stays near 1,500 as H shrinks, where fixed panels of length
-// 2 need 8 (30 + 7p)/H nodes (a faster precompute of the operators, the
-// paper's closing remark on quadrature rules).  sigma and k_z are computed at
-// the tail nodes (k_sigma).  buf holds the nodes until the next call.
-RuleNodes group_rule(fmm_layered* h, double H, double rho_max, DevBuf& buf, cudaStream_t st) {
-  Rule& R = h->rule;
-  const int L1 = h->L1, p = h->p;
+// 2 need 8 (30 + 7p)/H nodes.  group_tail appends the tail nodes and weights
+// (host); the group's block then holds n_near + that many nodes.
+int group_tail(const fmm_layered* h, double H, double rho_max, std::vector<cplx>& kr, std::vector<cplx>& w) {
+  const Rule& R = h->rule;
   std::vector<double> xg, wg;
   gauss_legendre(R.per_panel, xg, wg);
-  std::vector<cplx> kr, w;
-  const double tend = R.ta + (30.0 + 7.0 * p) / H;
+  const double tend = R.ta + (30.0 + 7.0 * h->p) / H;
   const double lmax = 4.0 / std::max(rho_max, H);
   double len = std::min(2.0, lmax), t = R.ta;
+  int n = 0;
   while (t < tend) {
     for (int i = 0; i < R.per_panel; ++i) {
       kr.push_back(C(t + 0.5 * len * (xg[i] + 1.0), 0.0));
       w.push_back(C(0.5 * len * wg[i], 0.0));
+      ++n;
     }
     t += len;
     len = std::min(1.5 * len, std::max(len, lmax));
   }
-  const int nn = R.n_near, Qg = nn + (int)kr.size();
-  const size_t nodes = (size_t)Qg * (2 + L1 + 4 * L1 * L1);
-  buf.ensure(sizeof(cplx) * nodes);
-  cplx* gkr = buf.as<cplx>();
-  cplx* gw = gkr + Qg;
-  cplx* gkz = gw + Qg;
-  cplx* gsig = gkz + (size_t)L1 * Qg;
-  FMM_CHECK(cudaMemcpyAsync(gkr + nn, kr.data(), sizeof(cplx) * kr.size(), cudaMemcpyHostToDevice, st));
-  FMM_CHECK(cudaMemcpyAsync(gw + nn, w.data(), sizeof(cplx) * w.size(), cudaMemcpyHostToDevice, st));
+  return n;
+}
+
+// Complete a group's node block whose tail kr, w are in place: copy the
+// handle's complex contour nodes in front and compute k_z and sigma at the
+// tail nodes (k_sigma).
+void group_rule_fill(fmm_layered* h, const RuleNodes& G, cudaStream_t st) {
+  Rule& R = h->rule;
+  const int L1 = h->L1, nn = G.n_near;
+  cplx* gkr = const_cast<cplx*>(G.kr);
+  cplx* gw = const_cast<cplx*>(G.w);
+  cplx* gkz = const_cast<cplx*>(G.kz);
+  cplx* gsig = const_cast<cplx*>(G.sigma);
   LAUNCH(k_rule_near_copy<<<(nn + 127) / 128, 128, 0, st>>>(L1, nn, R.Q(), R.kr.as<cplx>(), R.w.as<cplx>(),
-                                                             R.kz.as<cplx>(), R.sigma.as<cplx>(), Qg, gkr, gw, gkz,
+                                                             R.kz.as<cplx>(), R.sigma.as<cplx>(), G.Q, gkr, gw, gkz,
                                                              gsig));
-  dim3 grid((unsigned)((Qg - nn + 127) / 128), L1);
-  LAUNCH(k_sigma<<<grid, 128, 0, st>>>(L1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(), Qg, nn,
-                                       gkr, gkz, gsig));
+  if (G.Q > nn) {
+    dim3 grid((unsigned)((G.Q - nn + 127) / 128), L1);
+    LAUNCH(k_sigma<<<grid, 128, 0, st>>>(L1, h->d_k.as<double>(), h->d_d.as<double>(), h->d_eps.as<double>(), G.Q,
+                                         nn, gkr, gkz, gsig));
+  }
   FMM_CHECK(cudaGetLastError());
-  return RuleNodes{gkr, gw, gkz, gsig, Qg, nn};
 }

@@ -666,14 +666,21 @@ void launch_sep_ops(int p, const SepJob* jobs, int njobs, const double* G, cplx*
 }
 
 // Radial reaction M2L matrices of one group for nr radial classes.
+// scratch bytes of launch_reac_group for a group of Q nodes (n_near complex)
+// and nr radial classes
+size_t reac_group_scratch(int p, int Q, int n_near, int nr) {
+  const int P = (p + 1) * (p + 1), D = 2 * p + 1;
+  const int nn = std::min(n_near, Q), Qt = Q - nn;
+  return sizeof(cplx) * 2 * (size_t)nn * P + sizeof(double) * 2 * (size_t)Qt * P +
+         sizeof(cplx) * (size_t)nr * nn * D + sizeof(double) * (size_t)nr * Qt * D + 1024;
+}
+
 void launch_reac_group(int p, const ReacGroup& g, const RuleNodes& R, int nr, const double* d_rho,
                        const long* d_out_off, cplx* ops, DevBuf& scratch, cudaStream_t st) {
   const int P = (p + 1) * (p + 1);
   const int D = 2 * p + 1;
   const int nn = std::min(R.n_near, g.Q), Qt = g.Q - nn;
-  size_t bytes = sizeof(cplx) * 2 * (size_t)nn * P + sizeof(double) * 2 * (size_t)Qt * P +
-                 sizeof(cplx) * (size_t)nr * nn * D + sizeof(double) * (size_t)nr * Qt * D + 1024;
-  scratch.ensure(bytes);
+  scratch.ensure(reac_group_scratch(p, g.Q, R.n_near, nr));
   char* base = (char*)scratch.ptr;
   cplx* Ac = (cplx*)base;
   cplx* Bc = Ac + (size_t)nn * P;
