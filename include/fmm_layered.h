@@ -134,8 +134,7 @@ typedef struct {
   long   n_reac_T_nodes;   /* quadrature nodes summed over those integrals   */
   long   n_v_pairs_reac;   /* ... of n_v_pairs, in reaction components        */
   long   n_launches;       /* kernels of this library launched by the last
-                              evaluation (launches inside CUB's sort and scan
-                              calls not included)                            */
+                              evaluation (its own sort and scan included)    */
   double gpu_ms_m2l_gemm;  /* device time of the M2L translation products
                               alone (CUDA events around those launches)      */
   double m2l_gemm_flops;   /* their algorithmic flops: 8 per complex

@@ -286,8 +286,8 @@ struct fmm_layered {
   cudaEvent_t bdone = nullptr;
 };
 
-// Count of this library's kernel launches made by the calling host thread
-// (CUB's internal launches excluded).  Per thread, so that the problems of a
+// Count of this library's kernel launches made by the calling host thread.
+// Per thread, so that the problems of a
 // batched call, each evaluated by its own host thread, count their own.
 extern thread_local long g_fmm_launches;
 #define LAUNCH(...) do { ++g_fmm_launches; __VA_ARGS__; } while (0)
