@@ -81,8 +81,8 @@ def _direct_T(comp, p, rho, zt, zs, rule):
     return F.reaction_T_radial(MED, l, lp, a, b, p, rho, zt_abs, zs_abs, rule)
 
 
-@pytest.mark.parametrize("comp", [(0, 1, UP, DOWN), (2, 1, DOWN, DOWN), (1, 1, DOWN, UP), (0, 0, UP, UP)])
-@pytest.mark.parametrize("p", [5, 8])
+@pytest.mark.parametrize("comp,p", [((0, 1, UP, DOWN), 5), ((2, 1, DOWN, DOWN), 5), ((1, 1, DOWN, UP), 8),
+                                    ((0, 0, UP, UP), 8), ((0, 1, UP, DOWN), 10), ((2, 1, DOWN, DOWN), 12)])
 def test_s_expansion_reproduces_direct_operator(comp, p):
     l, lp = comp[0], comp[1]
     ex = tb.Expansion(p, MED.k[l], MED.k[lp])

@@ -28,7 +28,7 @@ def exe(tmp_path_factory):
     return str(out)
 
 
-@pytest.mark.parametrize("p,kl,klp,a", [(4, 0.8, 1.2, 0), (6, 1.6, 1.2, 1), (8, 1.2, 1.2, 0)])
+@pytest.mark.parametrize("p,kl,klp,a", [(4, 0.8, 1.2, 0), (6, 1.6, 1.2, 1), (8, 1.2, 1.2, 0), (12, 0.8, 1.6, 1)])
 def test_table_algebra_matches_oracle_expansion(exe, p, kl, klp, a):
     r = subprocess.run([exe, str(p), repr(kl), repr(klp), str(a)], capture_output=True, text=True, check=True)
     lines = r.stdout.strip().split("\n")
